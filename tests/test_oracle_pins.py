@@ -1,0 +1,388 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test ties the oracle to something other than itself: lattice isotropy,
+the moments of Eq. (feq), closed forms (isolated node, uniform flow, the
+exact discrete Poiseuille channel), a 1D recurrence derived by hand, exact
+mass conservation, symmetries, and a brute-force push-style BGK with full
+populations written here in plain Python.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import lbm_inputs
+import oracle
+
+
+LATTICES = (19, 27)
+
+
+# --------------------------------------------------------------------------
+# lattice tables and Eq. (feq)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("q", LATTICES)
+def test_lattice_isotropy(q):
+    """Weights and velocities satisfy the isotropy conditions of a c_s^2 = 1/3
+    lattice up to fourth order (Qian et al.), and inv(k) is the opposite."""
+    c, w, inv = oracle.lattice(q)
+    c = c.astype(np.float64)
+    assert math.isclose(math.fsum(w), 1.0, abs_tol=1e-15)
+    assert np.allclose(np.einsum("k,ka->a", w, c), 0.0, atol=1e-16)
+    second = np.einsum("k,ka,kb->ab", w, c, c)
+    assert np.allclose(second, np.eye(3) / 3.0, atol=1e-15)
+    assert np.allclose(np.einsum("k,ka,kb,kc->abc", w, c, c, c), 0.0, atol=1e-16)
+    d = np.eye(3)
+    fourth = np.einsum("k,ka,kb,kc,kd->abcd", w, c, c, c, c)
+    iso = (np.einsum("ab,cd->abcd", d, d) + np.einsum("ac,bd->abcd", d, d)
+           + np.einsum("ad,bc->abcd", d, d)) / 9.0
+    assert np.allclose(fourth, iso, atol=1e-15)
+    assert np.array_equal(c[inv], -c)
+    assert len({tuple(v) for v in c.astype(int)}) == q
+    # adjacent +/- pairs (the ordering the tables document)
+    for k in range(1, q):
+        assert inv[k] == (k + 1 if k % 2 == 1 else k - 1)
+
+
+@pytest.mark.parametrize("q", LATTICES)
+def test_feq_moments(q):
+    """Eq. (feq): sum f = rho, sum c f = rho v, sum c c f = rho (I/3 + v v)."""
+    c, w, _ = oracle.lattice(q)
+    c = c.astype(np.float64)
+    rng = np.random.default_rng(7)
+    for _ in range(20):
+        drho = rng.uniform(-0.05, 0.05)
+        v = rng.uniform(-0.08, 0.08, 3)
+        h = np.array([oracle.feq_dev(q, k, drho, *v) for k in range(q)])
+        f = h + w
+        rho = 1.0 + drho
+        assert abs(math.fsum(h) - drho) < 1e-16
+        assert np.allclose(c.T @ h, rho * v, rtol=0, atol=2e-16)
+        assert np.allclose(np.einsum("k,ka,kb->ab", f, c, c), rho * (np.eye(3) / 3 + np.outer(v, v)),
+                           rtol=0, atol=1e-15)
+    # the paper's form w rho (1 + 3cu + 4.5 (cu)^2 - 1.5 u.u), typed here
+    drho, v = 0.013, np.array([0.02, -0.011, 0.007])
+    for k in range(q):
+        cu = c[k] @ v
+        paper = w[k] * (1 + drho) * (1 + 3 * cu + 4.5 * cu * cu - 1.5 * v @ v)
+        assert abs((oracle.feq_dev(q, k, drho, *v) + w[k]) - paper) < 1e-16
+
+
+# --------------------------------------------------------------------------
+# closed forms
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("q", LATTICES)
+def test_isolated_fluid_node(q):
+    """All links bounced (halfway bounce-back on every link): rho' = rho and
+    u' = -(u + g) (Algorithm 'Complete Tau1 ... halfway bounce-back')."""
+    solid = np.ones((3, 3, 3), np.uint8)
+    solid[1, 1, 1] = 0
+    g = (1.1e-4, -2.3e-4, 0.7e-4)
+    D = oracle.Domain(q, solid, periodic=(1, 1, 1), g=g)
+    st = [np.zeros((3, 3, 3)) for _ in range(4)]
+    st[0][1, 1, 1], st[1][1, 1, 1], st[2][1, 1, 1], st[3][1, 1, 1] = 0.02, 0.011, -0.004, 0.006
+    out = D.tau1_step(st)
+    assert abs(out[0][1, 1, 1] - 0.02) < 1e-17
+    for a, (u, gg) in enumerate(zip((0.011, -0.004, 0.006), g)):
+        assert abs(out[1 + a][1, 1, 1] + (u + gg)) < 1e-17
+    assert all(np.count_nonzero(o) <= 1 for o in out)
+
+
+@pytest.mark.parametrize("q", LATTICES)
+def test_uniform_state_and_uniform_acceleration(q):
+    """No walls: a uniform state is a fixed point (g = 0) and under a body
+    force gains exactly g per step (sum c f^eq(v) = rho v)."""
+    shape = (4, 5, 6)
+    solid = np.zeros(shape, np.uint8)
+    u0 = np.array([0.01, -0.02, 0.005])
+    st = (np.full(shape, 0.03), np.full(shape, u0[0]), np.full(shape, u0[1]), np.full(shape, u0[2]))
+    D = oracle.Domain(q, solid, g=(0, 0, 0))
+    out = D.tau1_run(st, 50)
+    for a in range(4):
+        assert np.max(np.abs(out[a] - st[a])) < 1e-15
+    g = np.array([1e-5, 2e-5, -3e-5])
+    D = oracle.Domain(q, solid, g=g)
+    out = D.tau1_run(st, 50)
+    assert np.max(np.abs(out[0] - 0.03)) < 1e-15
+    for a in range(3):
+        assert np.max(np.abs(out[1 + a] - (u0[a] + 50 * g[a]))) < 1e-14
+
+
+def channel_recurrence(nz, g, nsteps):
+    """Hand-derived 1D reduction of the 3D channel (walls z=0 and z=nz-1,
+    uniform in x and y, rho = 1): with v = u + g,
+        interior  u'(z) = 2/3 v(z) + 1/6 (v(z-1) + v(z+1))
+        wall node u'(1) = 1/2 v(1) + 1/6 v(2), mirrored at z = nz-2.
+    Derived from Eq. (feq) summed over the layers c_z = -1, 0, 1 of D3Q19 and
+    D3Q27, whose sums of w c_x^2 are 1/18, 2/9, 1/18 for both lattices; the
+    quadratic terms cancel layer by layer."""
+    u = [0.0] * nz
+    for _ in range(nsteps):
+        v = [ui + g for ui in u]
+        new = [0.0] * nz
+        for z in range(1, nz - 1):
+            lo = v[z - 1] if z - 1 >= 1 else None
+            hi = v[z + 1] if z + 1 <= nz - 2 else None
+            if lo is None:
+                new[z] = 0.5 * v[z] + hi / 6.0
+            elif hi is None:
+                new[z] = 0.5 * v[z] + lo / 6.0
+            else:
+                new[z] = 2.0 / 3.0 * v[z] + (lo + hi) / 6.0
+        u = new
+    return np.array(u)
+
+
+@pytest.mark.parametrize("q", LATTICES)
+def test_channel_matches_1d_recurrence(q):
+    """The 32-high channel of the Poiseuille case, 1000 steps, reduces to the
+    1D recurrence at every step; every (x, y) column is the same."""
+    g = 1e-6
+    solid = lbm_inputs.channel(4, 3, 32)
+    D = oracle.Domain(q, solid, periodic=(1, 1, 0), g=(g, 0, 0))
+    out = D.tau1_run(D.zero_state(), 1000)
+    ref = channel_recurrence(32, g, 1000)
+    ux = out[1]
+    for y in range(3):
+        for x in range(4):
+            assert np.array_equal(ux[:, y, x], ux[:, 0, 0])
+    scale = np.max(np.abs(ref))
+    assert np.max(np.abs(ux[:, 0, 0] - ref)) <= 1e-12 * scale
+    assert np.max(np.abs(out[0])) < 1e-15
+    assert np.max(np.abs(out[2])) < 1e-18 and np.max(np.abs(out[3])) < 1e-18
+
+
+@pytest.mark.parametrize("q", LATTICES)
+def test_channel_steady_exact_discrete_poiseuille(q):
+    """Steady state of the channel: u(z) = 3 g (z - 1/2)(30.5 - z) - g/4, the
+    continuum profile of Eq. (poiseuile) with nu = 1/6, walls at z = 1/2 and
+    30.5, plus a uniform shift; rho = 1 and u_z = 0."""
+    g = 1e-6
+    solid = lbm_inputs.channel(2, 2, 32)
+    D = oracle.Domain(q, solid, periodic=(1, 1, 0), g=(g, 0, 0))
+    out = D.tau1_run(D.zero_state(), 20000)
+    z = np.arange(1, 31, dtype=np.float64)
+    exact = 3 * g * (z - 0.5) * (30.5 - z) - g / 4
+    ux = out[1][1:31, 0, 0]
+    assert np.max(np.abs(ux - exact)) <= 1e-12 * np.max(exact)
+    # continuum profile of Eq. (poiseuile) vs the physical velocity u + g/2
+    cont = g / (2 * oracle.NU) * (z - 0.5) * (30.5 - z)
+    mape = np.mean(np.abs((ux + g / 2) - cont) / cont)
+    assert mape < 1e-3
+    st = D.reduce(out)
+    assert st["n_fluid"] == 4 * 30
+    # Darcy permeability of a slit of width H = 30: H^2/12 * (30/32) (superficial) + slip
+    k_exact = float(np.sum(exact + g / 2)) / 32 / g * oracle.NU
+    assert abs(st["permeability"] - k_exact) < 1e-9 * k_exact
+
+
+# --------------------------------------------------------------------------
+# conservation and symmetry
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("q", LATTICES)
+@pytest.mark.parametrize("periodic", [(1, 1, 1), (1, 0, 1)])
+def test_mass_conservation(q, periodic):
+    """Every emitted population lands on exactly one fluid node (streamed or
+    bounced), so sum over fluid of drho is invariant: 1e-12 relative to the
+    fluid mass over 1000 steps."""
+    solid, _ = lbm_inputs.sphere_pack(16, 14, 12, 3.0, 0.7, seed=lbm_inputs.workload_seed(9, 1))
+    st = lbm_inputs.random_fields(solid.shape, 11, 1e-3, 1e-3, solid)
+    D = oracle.Domain(q, solid, periodic=periodic, g=(1e-5, 2e-6, -3e-6))
+    m0 = math.fsum(st[0][solid == 0])
+    out = D.tau1_run(st, 1000)
+    m1 = math.fsum(out[0][solid == 0])
+    nf = int(np.count_nonzero(solid == 0))
+    assert abs(m1 - m0) <= 1e-12 * nf
+    assert np.all(out[0][solid != 0] == 0) and np.all(out[1][solid != 0] == 0)
+
+
+@pytest.mark.parametrize("q", LATTICES)
+def test_translation_invariance_bitwise(q):
+    """Periodic shift of geometry and state gives the shifted result, bit for bit."""
+    shape = (7, 6, 9)
+    solid = lbm_inputs.random_mask(shape[2], shape[1], shape[0], 0.25, 5)
+    st = lbm_inputs.random_fields(shape, 6, 1e-3, 2e-3, solid)
+    D = oracle.Domain(q, solid, g=(1e-5, -2e-5, 3e-6))
+    ref = D.tau1_run(st, 5)
+    sh = (3, 2, 5)
+    D2 = oracle.Domain(q, np.roll(solid, sh, axis=(0, 1, 2)), g=(1e-5, -2e-5, 3e-6))
+    out = D2.tau1_run([np.roll(a, sh, axis=(0, 1, 2)) for a in st], 5)
+    for a in range(4):
+        assert np.array_equal(out[a], np.roll(ref[a], sh, axis=(0, 1, 2)))
+
+
+@pytest.mark.parametrize("q", LATTICES)
+def test_mirror_symmetry(q):
+    """x -> -x with u_x -> -u_x and g_x -> -g_x mirrors the result."""
+    shape = (6, 7, 8)
+    solid = lbm_inputs.random_mask(shape[2], shape[1], shape[0], 0.2, 8)
+    st = lbm_inputs.random_fields(shape, 9, 1e-3, 2e-3, solid)
+    g = np.array([2e-5, 1e-5, -1e-5])
+    ref = oracle.Domain(q, solid, periodic=(1, 0, 1), g=g).tau1_run(st, 6)
+    ms = np.ascontiguousarray(solid[:, :, ::-1])
+    mst = [np.ascontiguousarray(a[:, :, ::-1]) for a in st]
+    mst[1] = -mst[1]
+    out = oracle.Domain(q, ms, periodic=(1, 0, 1), g=g * np.array([-1, 1, 1])).tau1_run(mst, 6)
+    assert np.max(np.abs(out[0][:, :, ::-1] - ref[0])) < 1e-17
+    assert np.max(np.abs(-out[1][:, :, ::-1] - ref[1])) < 1e-17
+    assert np.max(np.abs(out[2][:, :, ::-1] - ref[2])) < 1e-17
+    assert np.max(np.abs(out[3][:, :, ::-1] - ref[3])) < 1e-17
+
+
+# --------------------------------------------------------------------------
+# Tau1 == BGK at tau = 1 (Eq. LBMTau1)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("q", LATTICES)
+@pytest.mark.parametrize("periodic", [(1, 1, 1), (0, 1, 1)])
+def test_tau1_equals_bgk_tau1(q, periodic):
+    """Standard pull BGK with stored populations, relaxed at tau = 1, and Tau1
+    give the same (rho, u) at every step, to rounding."""
+    solid, _ = lbm_inputs.sphere_pack(12, 10, 14, 2.5, 0.75, seed=3)
+    st = lbm_inputs.random_fields(solid.shape, 4, 2e-3, 3e-3, solid)
+    g = (1e-5, -4e-6, 2e-6)
+    D = oracle.Domain(q, solid, periodic=periodic, g=g)
+    h = D.bgk_init(st, 1.0)
+    t = st
+    worst = 0.0
+    for _ in range(200):
+        t = D.tau1_step(t)
+        h, b = D.bgk_step(h, 1.0)
+        for a in range(4):
+            worst = max(worst, float(np.max(np.abs(t[a] - b[a]))))
+    assert worst < 1e-16, worst
+
+
+def test_bgk_tau_not_one_differs():
+    """The BGK oracle honours tau: at tau != 1 it no longer equals Tau1 (so the
+    previous test is not a tautology of shared code)."""
+    solid, _ = lbm_inputs.sphere_pack(8, 8, 8, 2.0, 0.8, seed=5)
+    st = lbm_inputs.random_fields(solid.shape, 4, 2e-3, 3e-3, solid)
+    D = oracle.Domain(19, solid, g=(1e-5, 0, 0))
+    h = D.bgk_init(st, 0.8)
+    t = st
+    for _ in range(3):
+        t = D.tau1_step(t)
+        h, b = D.bgk_step(h, 0.8)
+    assert np.max(np.abs(t[1] - b[1])) > 1e-6
+
+
+# --------------------------------------------------------------------------
+# brute force: push-style BGK with full populations, plain Python
+# --------------------------------------------------------------------------
+
+def _brute_lattice(q):
+    vel = [(0, 0, 0)]
+    faces = [(1, 0, 0), (0, 1, 0), (0, 0, 1)]
+    edges = [(1, 1, 0), (1, -1, 0), (1, 0, 1), (1, 0, -1), (0, 1, 1), (0, 1, -1)]
+    corners = [(1, 1, 1), (1, 1, -1), (1, -1, 1), (-1, 1, 1)]
+    groups = [faces, edges] + ([corners] if q == 27 else [])
+    for grp in groups:
+        for v in grp:
+            vel.append(v)
+            vel.append(tuple(-a for a in v))
+    if q == 19:
+        wt = {0: 1 / 3, 1: 1 / 18, 2: 1 / 36}
+    else:
+        wt = {0: 8 / 27, 1: 2 / 27, 2: 1 / 54, 3: 1 / 216}
+    w = [wt[sum(a * a for a in v)] for v in vel]
+    return vel, w
+
+
+def brute_force_push(q, solid, periodic, g, state, nsteps):
+    """Full-population BGK at tau = 1, push streaming, halfway bounce-back:
+    a population pushed toward a wall returns to its node reversed."""
+    vel, w = _brute_lattice(q)
+    opp = [vel.index(tuple(-a for a in v)) for v in vel]
+    nz, ny, nx = solid.shape
+    dims = (nx, ny, nz)
+
+    def feq(k, rho, v):
+        cu = sum(vel[k][a] * v[a] for a in range(3))
+        vv = sum(a * a for a in v)
+        return w[k] * rho * (1 + 3 * cu + 4.5 * cu * cu - 1.5 * vv)
+
+    nodes = [(x, y, z) for z in range(nz) for y in range(ny) for x in range(nx) if not solid[z, y, x]]
+    f = {}
+    for (x, y, z) in nodes:
+        rho = 1 + state[0][z, y, x]
+        v = [state[1 + a][z, y, x] + g[a] for a in range(3)]
+        f[(x, y, z)] = [feq(k, rho, v) for k in range(q)]
+    out = None
+    for _ in range(nsteps):
+        new = {n: [0.0] * q for n in nodes}
+        for n in nodes:
+            for k in range(q):
+                d = [n[a] + vel[k][a] for a in range(3)]
+                wall = False
+                for a in range(3):
+                    if d[a] < 0 or d[a] >= dims[a]:
+                        if periodic[a]:
+                            d[a] %= dims[a]
+                        else:
+                            wall = True
+                if not wall and solid[d[2], d[1], d[0]]:
+                    wall = True
+                if wall:
+                    new[n][opp[k]] = f[n][k]
+                else:
+                    new[tuple(d)][k] = f[n][k]
+        out = [np.zeros(solid.shape) for _ in range(4)]
+        for n in nodes:
+            rho = sum(new[n])
+            j = [sum(vel[k][a] * new[n][k] for k in range(q)) for a in range(3)]
+            u = [j[a] / rho for a in range(3)]
+            x, y, z = n
+            out[0][z, y, x] = rho - 1
+            for a in range(3):
+                out[1 + a][z, y, x] = u[a]
+            f[n] = [feq(k, rho, [u[a] + g[a] for a in range(3)]) for k in range(q)]
+    return out
+
+
+@pytest.mark.parametrize("q", LATTICES)
+@pytest.mark.parametrize("case", [((4, 5, 3), (1, 1, 1), 0.3), ((5, 4, 4), (1, 0, 1), 0.2),
+                                  ((3, 3, 6), (0, 0, 1), 0.25)])
+def test_brute_force_push(q, case):
+    (nx, ny, nz), periodic, frac = case
+    solid = lbm_inputs.random_mask(nx, ny, nz, frac, 100 + nx)
+    st = lbm_inputs.random_fields(solid.shape, 200 + nz, 2e-2, 3e-2, solid)
+    g = (1e-3, -2e-3, 5e-4)
+    ref = brute_force_push(q, solid, periodic, g, st, 4)
+    out = oracle.Domain(q, solid, periodic=periodic, g=g).tau1_run(st, 4)
+    for a in range(4):
+        assert np.max(np.abs(out[a] - ref[a])) < 1e-14
+
+
+# --------------------------------------------------------------------------
+# sampled evaluation and reductions
+# --------------------------------------------------------------------------
+
+def test_nodes_matches_full_step():
+    solid, _ = lbm_inputs.sphere_pack(10, 9, 8, 2.0, 0.8, seed=12)
+    st = lbm_inputs.random_fields(solid.shape, 13, 1e-3, 1e-3, solid)
+    D = oracle.Domain(27, solid, periodic=(1, 1, 0), g=(1e-5, 0, 0))
+    full = D.tau1_step(st)
+    idx = np.array([0, 5, 77, 300, solid.size - 1])
+    got = D.tau1_nodes(st, idx)
+    for m, i in enumerate(idx):
+        for a in range(4):
+            assert got[m, a] == full[a].reshape(-1)[i]
+
+
+def test_reduce_definitions():
+    solid = lbm_inputs.random_mask(5, 4, 3, 0.3, 21)
+    st = lbm_inputs.random_fields(solid.shape, 22, 1e-3, 1e-3, solid)
+    g = np.array([2e-5, 0, 0])
+    r = oracle.Domain(19, solid, g=g).reduce(st)
+    fl = solid == 0
+    px = st[1] + g[0] / 2
+    assert r["n_fluid"] == int(fl.sum())
+    assert math.isclose(r["mass"], math.fsum((1 + st[0])[fl]), rel_tol=1e-15)
+    assert math.isclose(r["mean_ux_superficial"], math.fsum(px[fl]) / solid.size, rel_tol=1e-12)
+    mags = np.sqrt(px ** 2 + st[2] ** 2 + st[3] ** 2)[fl]
+    assert r["max_abs_u"] == pytest.approx(mags.max(), rel=1e-15)
+    assert r["permeability"] == pytest.approx(oracle.NU * r["mean_ux_superficial"] / g[0], rel=1e-15)
