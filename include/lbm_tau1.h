@@ -1,0 +1,163 @@
+/*
+ * lbm_tau1.h - C ABI of the GB300 Tau1 lattice Boltzmann solver.
+ *
+ * Tau1 (Bacza, Tomczak, Matyka, arXiv 2312.14742, Section 2.1, Eq. LBMTau1)
+ * is the BGK lattice Boltzmann method at relaxation time tau = 1, where the
+ * post-streaming populations equal the equilibria of the neighbours:
+ *     f_k(x, t+1) = f_k^eq(rho(x - c_k, t), u(x - c_k, t)).
+ * Only rho and u are stored (two ping-pong copies, Section 2.1.3 "Complexity
+ * analysis": 2 (d+1) s bytes per node). Each step gathers rho, u of the
+ * neighbours x - c_k, forms f_k^eq (Eq. feq, c_s^2 = 1/3), accumulates the
+ * new density and momentum, and multiplies the momentum once by 1/rho
+ * (Algorithm "Optimized Tau1 algorithm that stores velocity").
+ * Walls use halfway bounce-back from the node's own previous (rho*, u*)
+ * (Algorithm "Complete Tau1 algorithm with halfway bounce-back").
+ * The viscosity is fixed: nu = c_s^2 (tau - 1/2) = 1/6.
+ *
+ * Conventions for every entry point:
+ *  - Node index i = x + nx*(y + ny*z): x fastest.
+ *  - State is reported as drho = rho - 1 and u. Storing rho - 1 instead of
+ *    rho keeps the density signal in 32- and 16-bit storage.
+ *  - Body force g (lattice units) enters by velocity shift: every
+ *    equilibrium is evaluated at v = u + g. The stored u is the momentum of
+ *    the arriving populations over rho; the physical velocity is u + g/2.
+ *    The force is not in the paper (it drives its channel by pressure).
+ *  - A link x - c_k that is solid, or that leaves the box across a
+ *    non-periodic axis, is a wall.
+ *  - Solid nodes hold drho = 0 and u = 0.
+ *  - Every call returns an lbm_status; no C++ exception crosses the ABI. On
+ *    failure lbm_tau1_last_error() describes the cause.
+ *  - Host arrays passed in are read before the call returns and stay owned
+ *    by the caller. Device state belongs to the handle.
+ *  - A handle is not thread-safe; distinct handles are independent.
+ *  - Work is queued on the handle's CUDA stream. Calls that return host data
+ *    (get_fields to host, reduce) synchronise that stream.
+ */
+#ifndef LBM_TAU1_H
+#define LBM_TAU1_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_TAU1_ABI_VERSION 1
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_EINVAL = 1,     /* bad argument or configuration */
+    LBM_ENOMEM = 2,     /* device or host allocation failed */
+    LBM_ECUDA = 3,      /* a CUDA call failed (message in last_error) */
+    LBM_EDIVERGED = 4,  /* reduction saw a non-finite value or |u| > 0.3 */
+    LBM_ETIMEOUT = 5,   /* step cap reached before convergence */
+    LBM_EBUSY = 6,      /* no room (batch admission) */
+    LBM_ESTATE = 7      /* call out of order (e.g. step before set_geometry) */
+} lbm_status;
+
+typedef enum { LBM_D3Q19 = 19, LBM_D3Q27 = 27 } lbm_lattice;
+
+/* Storage of drho and u in device memory. F16S and BF16S hold each field
+ * times a power-of-two scale in 16 bits and compute in FP32. */
+typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16S = 2, LBM_BF16S = 3 } lbm_storage;
+
+typedef enum { LBM_DENSE = 0, LBM_SPARSE = 1 } lbm_layout;
+
+/* LBM_SCHEME_TAU1 is the method. LBM_SCHEME_BGK is the standard pull BGK at
+ * tau = 1 with stored populations in SoA form (Algorithm "Standard LBM",
+ * AB layout), kept as the comparison kernel; it supports LBM_F32 and
+ * LBM_F64 storage and the dense layout. */
+typedef enum { LBM_SCHEME_TAU1 = 0, LBM_SCHEME_BGK = 1 } lbm_scheme;
+
+/* Kernel choice for the dense Tau1 layout. AUTO picks the tiled kernel. */
+typedef enum { LBM_KERNEL_AUTO = 0, LBM_KERNEL_SIMPLE = 1, LBM_KERNEL_TILED = 2 } lbm_kernel;
+
+typedef struct lbm_tau1_config {
+    int32_t q;            /* lbm_lattice */
+    int32_t storage;      /* lbm_storage */
+    int32_t layout;       /* lbm_layout */
+    int32_t scheme;       /* lbm_scheme */
+    int32_t nx, ny, nz;   /* box size, each >= 1 */
+    uint8_t periodic[3];  /* 1 = periodic along x, y, z */
+    uint8_t kernel;       /* lbm_kernel */
+    double g[3];          /* body force per unit mass, lattice units */
+    void* cuda_stream;    /* cudaStream_t to queue work on; NULL = legacy default stream */
+} lbm_tau1_config;
+
+typedef struct lbm_tau1_stats {
+    int64_t step;                /* steps taken since set_geometry / set_fields */
+    int64_t n_nodes;             /* nx*ny*nz */
+    int64_t n_fluid;             /* fluid nodes */
+    int64_t nonfinite;           /* fluid nodes holding a non-finite value */
+    double mass;                 /* sum over fluid of rho */
+    double drho_sum;             /* sum over fluid of drho (mass - n_fluid, exact) */
+    double mean_ux_superficial;  /* sum over fluid of (u_x + g_x/2), divided by n_nodes */
+    double mean_u_fluid[3];      /* sum over fluid of (u + g/2), divided by n_fluid */
+    double max_abs_u;            /* max over fluid of |u + g/2| */
+    double permeability;         /* nu * mean_ux_superficial / g_x, nu = 1/6 (Darcy); NaN if g_x == 0 */
+} lbm_tau1_stats;
+
+typedef struct lbm_tau1 lbm_tau1;  /* opaque, owned by the library */
+
+/* ABI version of the loaded library (LBM_TAU1_ABI_VERSION it was built with). */
+int32_t lbm_tau1_abi_version(void);
+
+/* Validates cfg, allocates the device state of one box on cfg->cuda_stream
+ * (two copies of drho, ux, uy, uz in the storage type, a uint8 node-flag
+ * array, reduction scratch) and returns the handle in *out.
+ * Errors: LBM_EINVAL (bad cfg or NULL), LBM_ENOMEM, LBM_ECUDA. On error
+ * *out is NULL and lbm_tau1_last_error(NULL) gives the message. */
+lbm_status lbm_tau1_create(const lbm_tau1_config* cfg, lbm_tau1** out);
+
+/* Sets the geometry: solid has nx*ny*nz bytes, 1 = solid, 0 = fluid, node
+ * index x + nx*(y + ny*z). on_device != 0: solid is a device pointer readable
+ * on the handle's stream; else a host pointer. Classifies nodes, builds the
+ * kernel's wall-link data and resets the state to drho = 0, u = 0 on every
+ * node (the paper's rho = 1, u = 0 start) and the step counter to 0.
+ * Errors: LBM_EINVAL, LBM_ECUDA. */
+lbm_status lbm_tau1_set_geometry(lbm_tau1* h, const uint8_t* solid, int on_device);
+
+/* Overwrites the state with drho, ux, uy, uz (nx*ny*nz doubles each, host
+ * or device per on_device). Values on solid nodes are ignored (kept 0).
+ * For 16-bit storage the per-field scales are chosen from these values.
+ * Resets the step counter to 0. Requires set_geometry first (LBM_ESTATE). */
+lbm_status lbm_tau1_set_fields(lbm_tau1* h, const double* drho, const double* ux,
+                               const double* uy, const double* uz, int on_device);
+
+/* Copies the current state out as doubles (nx*ny*nz each, host or device per
+ * on_device). Any pointer may be NULL to skip that field. Host copies
+ * synchronise the handle's stream. Requires set_geometry (LBM_ESTATE). */
+lbm_status lbm_tau1_get_fields(lbm_tau1* h, double* drho, double* ux, double* uy,
+                               double* uz, int on_device);
+
+/* Queues nsteps >= 0 Tau1 steps (or BGK steps for LBM_SCHEME_BGK) on the
+ * handle's stream and returns without waiting. Each step reads the current
+ * copy and writes the other; the copies swap on the host.
+ * Errors: LBM_EINVAL (nsteps < 0), LBM_ESTATE (no geometry), LBM_ECUDA. */
+lbm_status lbm_tau1_step(lbm_tau1* h, int64_t nsteps);
+
+/* FP64 global reductions of the current state into *out (see
+ * lbm_tau1_stats). Deterministic: a fixed two-pass block tree. Synchronises
+ * the handle's stream. Returns LBM_EDIVERGED (with *out filled) when a fluid
+ * node is non-finite or max|u + g/2| > 0.3. */
+lbm_status lbm_tau1_reduce(lbm_tau1* h, lbm_tau1_stats* out);
+
+/* Waits for all work queued on the handle's stream. */
+lbm_status lbm_tau1_synchronize(lbm_tau1* h);
+
+/* Frees the handle and its device memory (after synchronising). NULL is a no-op. */
+lbm_status lbm_tau1_destroy(lbm_tau1* h);
+
+/* Last error message of h, or of the calling thread's last failed create
+ * when h is NULL. Never NULL; valid until the next call on h. */
+const char* lbm_tau1_last_error(const lbm_tau1* h);
+
+/* Number of device kernel launches queued by this handle since creation. */
+int64_t lbm_tau1_launch_count(const lbm_tau1* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_TAU1_H */

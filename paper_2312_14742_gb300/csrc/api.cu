@@ -1,0 +1,343 @@
+// C ABI of the Tau1 solver: handle life cycle, geometry, state I/O, stepping
+// and reductions. Declarations and the contract of each entry point are in
+// include/lbm_tau1.h.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "kernels.h"
+#include "lbm_tau1.h"
+
+using namespace lbm;
+
+struct lbm_tau1 {
+    lbm_tau1_config cfg{};
+    cudaStream_t stream = nullptr;
+    int64_t n = 0;
+    size_t elem = 0;            // bytes per stored scalar
+    void* buf[2][4] = {};       // ping-pong copies of drho, ux, uy, uz
+    int cur = 0;                // buf[cur] is the current (pre) state
+    uint8_t* flags = nullptr;   // node flags
+    double* red_partials = nullptr;
+    double* red_out = nullptr;  // device, RED_FIELDS doubles
+    double* red_host = nullptr; // pinned host copy of red_out
+    bool has_geometry = false;
+    int64_t step = 0;
+    int64_t n_fluid = -1;
+    float scale[4] = {1, 1, 1, 1};
+    float inv_scale[4] = {1, 1, 1, 1};
+    int kernel = LBM_KERNEL_SIMPLE;
+    int64_t launches = 0;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+lbm_status fail(lbm_tau1* h, lbm_status st, const std::string& msg)
+{
+    if (h) h->err = msg;
+    else g_create_error = msg;
+    return st;
+}
+
+lbm_status cuda_fail(lbm_tau1* h, cudaError_t e, const char* what)
+{
+    std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return fail(h, e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, m);
+}
+
+#define LBM_CUDA(h, call, what)                          \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, what); \
+    } while (0)
+
+size_t storage_bytes(int st)
+{
+    switch (st) {
+    case LBM_F64: return 8;
+    case LBM_F32: return 4;
+    case LBM_F16S:
+    case LBM_BF16S: return 2;
+    default: return 0;
+    }
+}
+
+void free_all(lbm_tau1* h)
+{
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    for (int b = 0; b < 2; ++b)
+        for (int f = 0; f < 4; ++f)
+            if (h->buf[b][f]) cudaFree(h->buf[b][f]);
+    if (h->flags) cudaFree(h->flags);
+    if (h->red_partials) cudaFree(h->red_partials);
+    if (h->red_out) cudaFree(h->red_out);
+    if (h->red_host) cudaFreeHost(h->red_host);
+}
+
+lbm_status check_ptr(lbm_tau1* h, const void* p, int on_device, const char* name)
+{
+    if (!p) return LBM_OK;
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) { cudaGetLastError(); return fail(h, LBM_EINVAL, std::string(name) + ": unknown pointer"); }
+    const bool dev = at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (on_device && !dev) return fail(h, LBM_EINVAL, std::string(name) + ": on_device=1 but not a device pointer");
+    return LBM_OK;
+}
+
+lbm_status launch_step(lbm_tau1* h)
+{
+    StepArgs a;
+    a.nx = h->cfg.nx;
+    a.ny = h->cfg.ny;
+    a.nz = h->cfg.nz;
+    for (int d = 0; d < 3; ++d) { a.periodic[d] = h->cfg.periodic[d] ? 1 : 0; a.g[d] = h->cfg.g[d]; }
+    a.flags = h->flags;
+    for (int f = 0; f < 4; ++f) {
+        a.pre[f] = h->buf[h->cur][f];
+        a.post[f] = h->buf[h->cur ^ 1][f];
+        a.inv_scale[f] = h->inv_scale[f];
+        a.scale[f] = h->scale[f];
+    }
+    cudaError_t e;
+    if (h->kernel == LBM_KERNEL_TILED) e = launch_tau1_tiled(h->cfg.q, h->cfg.storage, a, h->stream);
+    else e = launch_tau1_simple(h->cfg.q, h->cfg.storage, a, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "tau1 step launch");
+    ++h->launches;
+    h->cur ^= 1;
+    ++h->step;
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t lbm_tau1_abi_version(void) { return LBM_TAU1_ABI_VERSION; }
+
+const char* lbm_tau1_last_error(const lbm_tau1* h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+int64_t lbm_tau1_launch_count(const lbm_tau1* h) { return h ? h->launches : 0; }
+
+lbm_status lbm_tau1_create(const lbm_tau1_config* cfg, lbm_tau1** out)
+{
+    if (out) *out = nullptr;
+    if (!cfg || !out) return fail(nullptr, LBM_EINVAL, "create: NULL argument");
+    if (cfg->q != 19 && cfg->q != 27) return fail(nullptr, LBM_EINVAL, "create: q must be 19 or 27");
+    if (storage_bytes(cfg->storage) == 0) return fail(nullptr, LBM_EINVAL, "create: bad storage");
+    if (cfg->nx < 1 || cfg->ny < 1 || cfg->nz < 1) return fail(nullptr, LBM_EINVAL, "create: box sizes must be >= 1");
+    if (cfg->layout != LBM_DENSE) return fail(nullptr, LBM_EINVAL, "create: only the dense layout is available");
+    if (cfg->scheme != LBM_SCHEME_TAU1) return fail(nullptr, LBM_EINVAL, "create: scheme not available");
+    if (cfg->kernel > LBM_KERNEL_TILED) return fail(nullptr, LBM_EINVAL, "create: bad kernel");
+    for (int d = 0; d < 3; ++d)
+        if (!std::isfinite(cfg->g[d])) return fail(nullptr, LBM_EINVAL, "create: g must be finite");
+    const int64_t n = (int64_t)cfg->nx * cfg->ny * cfg->nz;
+    if (n > ((int64_t)1 << 33)) return fail(nullptr, LBM_EINVAL, "create: box too large");
+
+    lbm_tau1* h = new (std::nothrow) lbm_tau1();
+    if (!h) return fail(nullptr, LBM_ENOMEM, "create: host allocation failed");
+    h->cfg = *cfg;
+    h->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
+    h->n = n;
+    h->elem = storage_bytes(cfg->storage);
+    h->kernel = cfg->kernel;
+    if (h->kernel == LBM_KERNEL_AUTO)
+        h->kernel = tau1_tiled_supported(cfg->q, cfg->storage) ? LBM_KERNEL_TILED : LBM_KERNEL_SIMPLE;
+    if (h->kernel == LBM_KERNEL_TILED && !tau1_tiled_supported(cfg->q, cfg->storage)) {
+        delete h;
+        return fail(nullptr, LBM_EINVAL, "create: tiled kernel not available for this lattice/storage");
+    }
+    cudaError_t e = cudaSuccess;
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b)
+        for (int f = 0; f < 4 && e == cudaSuccess; ++f) e = cudaMalloc(&h->buf[b][f], (size_t)n * h->elem);
+    if (e == cudaSuccess) e = cudaMalloc(&h->flags, (size_t)n);
+    if (e == cudaSuccess) e = cudaMalloc(&h->red_partials, (size_t)reduce_blocks(n) * RED_FIELDS * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&h->red_out, RED_FIELDS * sizeof(double));
+    if (e == cudaSuccess) e = cudaMallocHost(&h->red_host, RED_FIELDS * sizeof(double));
+    if (e != cudaSuccess) {
+        lbm_status st = cuda_fail(nullptr, e, "create: device allocation");
+        free_all(h);
+        delete h;
+        return st;
+    }
+    *out = h;
+    return LBM_OK;
+}
+
+lbm_status lbm_tau1_destroy(lbm_tau1* h)
+{
+    if (!h) return LBM_OK;
+    free_all(h);
+    delete h;
+    return LBM_OK;
+}
+
+lbm_status lbm_tau1_synchronize(lbm_tau1* h)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "synchronize: NULL handle");
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream), "synchronize");
+    return LBM_OK;
+}
+
+lbm_status lbm_tau1_set_geometry(lbm_tau1* h, const uint8_t* solid, int on_device)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "set_geometry: NULL handle");
+    if (!solid) return fail(h, LBM_EINVAL, "set_geometry: NULL mask");
+    if (lbm_status st = check_ptr(h, solid, on_device, "set_geometry mask")) return st;
+    const uint8_t* dsolid = solid;
+    uint8_t* tmp = nullptr;
+    if (!on_device) {
+        LBM_CUDA(h, cudaMallocAsync((void**)&tmp, (size_t)h->n, h->stream), "set_geometry: staging allocation");
+        LBM_CUDA(h, cudaMemcpyAsync(tmp, solid, (size_t)h->n, cudaMemcpyDefault, h->stream), "set_geometry: copy");
+        dsolid = tmp;
+    }
+    int per[3] = {h->cfg.periodic[0] ? 1 : 0, h->cfg.periodic[1] ? 1 : 0, h->cfg.periodic[2] ? 1 : 0};
+    cudaError_t e = launch_build_flags(h->cfg.q, h->cfg.nx, h->cfg.ny, h->cfg.nz, per, dsolid, h->flags, h->stream);
+    ++h->launches;
+    if (tmp) cudaFreeAsync(tmp, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "set_geometry: flags kernel");
+    for (int b = 0; b < 2; ++b)
+        for (int f = 0; f < 4; ++f)
+            LBM_CUDA(h, cudaMemsetAsync(h->buf[b][f], 0, (size_t)h->n * h->elem, h->stream), "set_geometry: clear");
+    for (int f = 0; f < 4; ++f) h->scale[f] = h->inv_scale[f] = 1.0f;
+    h->cur = 0;
+    h->step = 0;
+    h->n_fluid = -1;
+    h->has_geometry = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_tau1_set_fields(lbm_tau1* h, const double* drho, const double* ux, const double* uy,
+                               const double* uz, int on_device)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "set_fields: NULL handle");
+    if (!h->has_geometry) return fail(h, LBM_ESTATE, "set_fields: call set_geometry first");
+    const double* src[4] = {drho, ux, uy, uz};
+    for (int f = 0; f < 4; ++f) {
+        if (!src[f]) return fail(h, LBM_EINVAL, "set_fields: NULL field");
+        if (lbm_status st = check_ptr(h, src[f], on_device, "set_fields field")) return st;
+    }
+    const size_t bytes = (size_t)h->n * sizeof(double);
+    double* tmp = nullptr;
+    const double* dsrc[4];
+    if (!on_device) {
+        LBM_CUDA(h, cudaMallocAsync((void**)&tmp, 4 * bytes, h->stream), "set_fields: staging allocation");
+        for (int f = 0; f < 4; ++f) {
+            LBM_CUDA(h, cudaMemcpyAsync(tmp + f * h->n, src[f], bytes, cudaMemcpyDefault, h->stream),
+                     "set_fields: copy");
+            dsrc[f] = tmp + f * h->n;
+        }
+    } else {
+        for (int f = 0; f < 4; ++f) dsrc[f] = src[f];
+    }
+    if (h->cfg.storage == LBM_F16S || h->cfg.storage == LBM_BF16S) {
+        // power-of-two scale putting the largest |value| near 2^12 (FP16 max ~2^16)
+        int blocks = reduce_blocks(h->n);
+        cudaError_t e = launch_absmax_f64(h->n, dsrc, h->flags, h->red_out, h->red_partials, blocks, h->stream);
+        h->launches += 2;
+        if (e != cudaSuccess) return cuda_fail(h, e, "set_fields: absmax");
+        LBM_CUDA(h, cudaMemcpyAsync(h->red_host, h->red_out, 4 * sizeof(double), cudaMemcpyDefault, h->stream),
+                 "set_fields: absmax copy");
+        LBM_CUDA(h, cudaStreamSynchronize(h->stream), "set_fields: sync");
+        for (int f = 0; f < 4; ++f) {
+            const double m = h->red_host[f];
+            int ex = 0;
+            if (m > 0 && std::isfinite(m)) { std::frexp(m, &ex); ex = 12 - ex; }
+            if (h->cfg.storage == LBM_BF16S) ex = 0;
+            if (ex > 100) ex = 100;
+            if (ex < -100) ex = -100;
+            h->scale[f] = std::ldexp(1.0f, ex);
+            h->inv_scale[f] = std::ldexp(1.0f, -ex);
+        }
+    }
+    void* dst[4];
+    for (int f = 0; f < 4; ++f) dst[f] = h->buf[h->cur][f];
+    cudaError_t e = launch_import_fields(h->cfg.storage, h->n, dsrc, dst, h->flags, h->scale, h->stream);
+    ++h->launches;
+    if (tmp) cudaFreeAsync(tmp, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "set_fields: import kernel");
+    h->step = 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_tau1_get_fields(lbm_tau1* h, double* drho, double* ux, double* uy, double* uz, int on_device)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "get_fields: NULL handle");
+    if (!h->has_geometry) return fail(h, LBM_ESTATE, "get_fields: call set_geometry first");
+    double* dst[4] = {drho, ux, uy, uz};
+    for (int f = 0; f < 4; ++f)
+        if (lbm_status st = check_ptr(h, dst[f], on_device, "get_fields field")) return st;
+    const size_t bytes = (size_t)h->n * sizeof(double);
+    double* tmp = nullptr;
+    LBM_CUDA(h, cudaMallocAsync((void**)&tmp, 4 * bytes, h->stream), "get_fields: staging allocation");
+    double* ddst[4];
+    for (int f = 0; f < 4; ++f) ddst[f] = (on_device && dst[f]) ? dst[f] : tmp + f * h->n;
+    const void* src[4];
+    for (int f = 0; f < 4; ++f) src[f] = h->buf[h->cur][f];
+    cudaError_t e = launch_export_fields(h->cfg.storage, h->n, src, ddst, h->inv_scale, h->stream);
+    ++h->launches;
+    if (e != cudaSuccess) { cudaFreeAsync(tmp, h->stream); return cuda_fail(h, e, "get_fields: export kernel"); }
+    if (!on_device) {
+        for (int f = 0; f < 4; ++f)
+            if (dst[f]) {
+                e = cudaMemcpyAsync(dst[f], ddst[f], bytes, cudaMemcpyDefault, h->stream);
+                if (e != cudaSuccess) { cudaFreeAsync(tmp, h->stream); return cuda_fail(h, e, "get_fields: copy"); }
+            }
+    }
+    cudaFreeAsync(tmp, h->stream);
+    if (!on_device) LBM_CUDA(h, cudaStreamSynchronize(h->stream), "get_fields: sync");
+    return LBM_OK;
+}
+
+lbm_status lbm_tau1_step(lbm_tau1* h, int64_t nsteps)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "step: NULL handle");
+    if (nsteps < 0) return fail(h, LBM_EINVAL, "step: nsteps < 0");
+    if (!h->has_geometry) return fail(h, LBM_ESTATE, "step: call set_geometry first");
+    for (int64_t t = 0; t < nsteps; ++t)
+        if (lbm_status st = launch_step(h)) return st;
+    return LBM_OK;
+}
+
+lbm_status lbm_tau1_reduce(lbm_tau1* h, lbm_tau1_stats* out)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "reduce: NULL handle");
+    if (!out) return fail(h, LBM_EINVAL, "reduce: NULL output");
+    if (!h->has_geometry) return fail(h, LBM_ESTATE, "reduce: call set_geometry first");
+    const void* f[4];
+    for (int a = 0; a < 4; ++a) f[a] = h->buf[h->cur][a];
+    cudaError_t e = launch_reduce(h->cfg.storage, h->n, f, h->inv_scale, h->flags, h->cfg.g, h->red_partials,
+                                  h->red_out, h->stream);
+    h->launches += 2;
+    if (e != cudaSuccess) return cuda_fail(h, e, "reduce: kernel");
+    LBM_CUDA(h, cudaMemcpyAsync(h->red_host, h->red_out, RED_FIELDS * sizeof(double), cudaMemcpyDefault,
+                                h->stream), "reduce: copy");
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream), "reduce: sync");
+    const double* r = h->red_host;
+    std::memset(out, 0, sizeof(*out));
+    out->step = h->step;
+    out->n_nodes = h->n;
+    out->n_fluid = (int64_t)r[RED_NFLUID];
+    out->nonfinite = (int64_t)r[RED_NONFINITE];
+    out->drho_sum = r[RED_DRHO];
+    out->mass = (double)out->n_fluid + r[RED_DRHO];
+    out->mean_ux_superficial = r[RED_PX] / (double)h->n;
+    const double nf = out->n_fluid > 0 ? (double)out->n_fluid : 1.0;
+    out->mean_u_fluid[0] = r[RED_PX] / nf;
+    out->mean_u_fluid[1] = r[RED_PY] / nf;
+    out->mean_u_fluid[2] = r[RED_PZ] / nf;
+    out->max_abs_u = r[RED_UMAX];
+    out->permeability = h->cfg.g[0] != 0.0 ? (1.0 / 6.0) * out->mean_ux_superficial / h->cfg.g[0] : NAN;
+    h->n_fluid = out->n_fluid;
+    if (out->nonfinite > 0 || out->max_abs_u > 0.3)
+        return fail(h, LBM_EDIVERGED, "reduce: state diverged (non-finite value or |u| > 0.3)");
+    return LBM_OK;
+}
+
+}  // extern "C"

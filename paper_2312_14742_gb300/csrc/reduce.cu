@@ -1,0 +1,131 @@
+// Deterministic FP64 global reductions of one box's state.
+//
+// Pass 1: block b owns a fixed contiguous range of nodes; each thread sums a
+// fixed strided subset, then a fixed shared-memory tree combines the block
+// (warp shuffles for the last 32). Pass 2: one block combines the per-block
+// partials in the same fixed way. The order of every addition depends only
+// on n, so repeated calls give identical bits.
+//
+// Per fluid node: count, drho, physical velocity u + g/2 (three sums), the
+// max of |u + g/2|, and a count of non-finite values.
+#include "kernels.h"
+
+namespace lbm {
+
+static constexpr int RT = 256;  // threads per reduction block
+
+int reduce_blocks(int64_t n)
+{
+    int64_t b = (n + 4095) / 4096;
+    if (b < 1) b = 1;
+    if (b > 1024) b = 1024;
+    return (int)b;
+}
+
+struct Fields4 {
+    const void* p[4];
+};
+struct Sc4r {
+    float v[4];
+};
+
+__device__ __forceinline__ void combine(double* a, const double* b)
+{
+#pragma unroll
+    for (int f = 0; f < RED_FIELDS; ++f) a[f] = (f == RED_UMAX) ? fmax(a[f], b[f]) : a[f] + b[f];
+}
+
+// Fixed-shape block reduction of RED_FIELDS doubles per thread; result in v of thread 0.
+__device__ __forceinline__ void block_reduce(double* v, double (*sm)[RT])
+{
+#pragma unroll
+    for (int f = 0; f < RED_FIELDS; ++f) sm[f][threadIdx.x] = v[f];
+    __syncthreads();
+    for (int w = RT / 2; w >= 32; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            double o[RED_FIELDS];
+#pragma unroll
+            for (int f = 0; f < RED_FIELDS; ++f) { v[f] = sm[f][threadIdx.x]; o[f] = sm[f][threadIdx.x + w]; }
+            combine(v, o);
+#pragma unroll
+            for (int f = 0; f < RED_FIELDS; ++f) sm[f][threadIdx.x] = v[f];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 32) {
+#pragma unroll
+        for (int f = 0; f < RED_FIELDS; ++f) v[f] = sm[f][threadIdx.x];
+        for (int off = 16; off > 0; off >>= 1) {
+            double o[RED_FIELDS];
+#pragma unroll
+            for (int f = 0; f < RED_FIELDS; ++f) o[f] = __shfl_down_sync(0xffffffffu, v[f], off);
+            combine(v, o);
+        }
+    }
+}
+
+template <int ST>
+__global__ void __launch_bounds__(RT) reduce_pass1(int64_t n, Fields4 fl, Sc4r inv, const uint8_t* __restrict__ flags,
+                                                   double hgx, double hgy, double hgz, double* __restrict__ partials)
+{
+    using S = Storage<ST>;
+    using st = typename S::stype;
+    __shared__ double sm[RED_FIELDS][RT];
+    const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t lo = (int64_t)blockIdx.x * per;
+    const int64_t hi = lo + per < n ? lo + per : n;
+    double v[RED_FIELDS] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int64_t i = lo + threadIdx.x; i < hi; i += RT) {
+        if (flags[i] & FLAG_SOLID) continue;
+        const double d = (double)S::load(static_cast<const st*>(fl.p[0]), i, inv.v[0]);
+        const double px = (double)S::load(static_cast<const st*>(fl.p[1]), i, inv.v[1]) + hgx;
+        const double py = (double)S::load(static_cast<const st*>(fl.p[2]), i, inv.v[2]) + hgy;
+        const double pz = (double)S::load(static_cast<const st*>(fl.p[3]), i, inv.v[3]) + hgz;
+        v[RED_NFLUID] += 1.0;
+        v[RED_DRHO] += d;
+        v[RED_PX] += px;
+        v[RED_PY] += py;
+        v[RED_PZ] += pz;
+        const double m = sqrt(px * px + py * py + pz * pz);
+        if (isfinite(d) && isfinite(m)) v[RED_UMAX] = fmax(v[RED_UMAX], m);
+        else v[RED_NONFINITE] += 1.0;
+    }
+    block_reduce(v, sm);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int f = 0; f < RED_FIELDS; ++f) partials[(int64_t)blockIdx.x * RED_FIELDS + f] = v[f];
+}
+
+__global__ void __launch_bounds__(RT) reduce_pass2(int blocks, const double* __restrict__ partials, double* __restrict__ out)
+{
+    __shared__ double sm[RED_FIELDS][RT];
+    double v[RED_FIELDS] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int b = threadIdx.x; b < blocks; b += RT) combine(v, partials + (int64_t)b * RED_FIELDS);
+    block_reduce(v, sm);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int f = 0; f < RED_FIELDS; ++f) out[f] = v[f];
+}
+
+cudaError_t launch_reduce(int storage, int64_t n, const void* const fields[4], const float inv_scale[4],
+                          const uint8_t* flags, const double g[3], double* partials, double* out, cudaStream_t s)
+{
+    Fields4 f;
+    Sc4r sc;
+    for (int a = 0; a < 4; ++a) { f.p[a] = fields[a]; sc.v[a] = inv_scale[a]; }
+    const int blocks = reduce_blocks(n);
+    const double hx = 0.5 * g[0], hy = 0.5 * g[1], hz = 0.5 * g[2];
+    switch (storage) {
+    case ST_F64: reduce_pass1<ST_F64><<<blocks, RT, 0, s>>>(n, f, sc, flags, hx, hy, hz, partials); break;
+    case ST_F32: reduce_pass1<ST_F32><<<blocks, RT, 0, s>>>(n, f, sc, flags, hx, hy, hz, partials); break;
+    case ST_F16S: reduce_pass1<ST_F16S><<<blocks, RT, 0, s>>>(n, f, sc, flags, hx, hy, hz, partials); break;
+    case ST_BF16S: reduce_pass1<ST_BF16S><<<blocks, RT, 0, s>>>(n, f, sc, flags, hx, hy, hz, partials); break;
+    default: return cudaErrorInvalidValue;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    reduce_pass2<<<1, RT, 0, s>>>(blocks, partials, out);
+    return cudaGetLastError();
+}
+
+}  // namespace lbm

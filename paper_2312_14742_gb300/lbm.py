@@ -1,0 +1,255 @@
+"""Python binding of liblbm_tau1.so (ctypes; argument marshalling only).
+
+Every function named ``lbm_tau1_*`` here calls the C entry point of the same
+name in include/lbm_tau1.h. ``Tau1`` is a thin owner of one handle that
+accepts numpy arrays (host) or torch CUDA tensors (device) and raises
+``LbmError`` on a non-OK status. All arithmetic runs in the CUDA kernels;
+when the library is missing, ``load()`` raises instead of falling back.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LIB_PATH = _build.LIB
+
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EDIVERGED, LBM_ETIMEOUT, LBM_EBUSY, LBM_ESTATE = range(8)
+STATUS_NAMES = ["LBM_OK", "LBM_EINVAL", "LBM_ENOMEM", "LBM_ECUDA", "LBM_EDIVERGED", "LBM_ETIMEOUT", "LBM_EBUSY",
+                "LBM_ESTATE"]
+LBM_D3Q19, LBM_D3Q27 = 19, 27
+LBM_F64, LBM_F32, LBM_F16S, LBM_BF16S = range(4)
+STORAGE = {"f64": LBM_F64, "f32": LBM_F32, "f16s": LBM_F16S, "bf16s": LBM_BF16S}
+LBM_DENSE, LBM_SPARSE = 0, 1
+LBM_SCHEME_TAU1, LBM_SCHEME_BGK = 0, 1
+LBM_KERNEL_AUTO, LBM_KERNEL_SIMPLE, LBM_KERNEL_TILED = 0, 1, 2
+KERNELS = {"auto": LBM_KERNEL_AUTO, "simple": LBM_KERNEL_SIMPLE, "tiled": LBM_KERNEL_TILED}
+
+
+class lbm_tau1_config(ctypes.Structure):
+    _fields_ = [("q", ctypes.c_int32), ("storage", ctypes.c_int32), ("layout", ctypes.c_int32),
+                ("scheme", ctypes.c_int32), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("periodic", ctypes.c_uint8 * 3), ("kernel", ctypes.c_uint8), ("g", ctypes.c_double * 3),
+                ("cuda_stream", ctypes.c_void_p)]
+
+
+class lbm_tau1_stats(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_int64), ("n_nodes", ctypes.c_int64), ("n_fluid", ctypes.c_int64),
+                ("nonfinite", ctypes.c_int64), ("mass", ctypes.c_double), ("drho_sum", ctypes.c_double),
+                ("mean_ux_superficial", ctypes.c_double), ("mean_u_fluid", ctypes.c_double * 3),
+                ("max_abs_u", ctypes.c_double), ("permeability", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {"step": self.step, "n_nodes": self.n_nodes, "n_fluid": self.n_fluid, "nonfinite": self.nonfinite,
+                "mass": self.mass, "drho_sum": self.drho_sum, "mean_ux_superficial": self.mean_ux_superficial,
+                "mean_u_fluid": tuple(self.mean_u_fluid), "max_abs_u": self.max_abs_u,
+                "permeability": self.permeability}
+
+
+_H = ctypes.c_void_p
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_I64 = ctypes.c_int64
+
+# name -> (restype, argtypes); every function declared in include/lbm_tau1.h
+SIGNATURES = {
+    "lbm_tau1_abi_version": (ctypes.c_int32, []),
+    "lbm_tau1_create": (_I, [ctypes.POINTER(lbm_tau1_config), ctypes.POINTER(_H)]),
+    "lbm_tau1_set_geometry": (_I, [_H, _P, _I]),
+    "lbm_tau1_set_fields": (_I, [_H, _P, _P, _P, _P, _I]),
+    "lbm_tau1_get_fields": (_I, [_H, _P, _P, _P, _P, _I]),
+    "lbm_tau1_step": (_I, [_H, _I64]),
+    "lbm_tau1_reduce": (_I, [_H, ctypes.POINTER(lbm_tau1_stats)]),
+    "lbm_tau1_synchronize": (_I, [_H]),
+    "lbm_tau1_destroy": (_I, [_H]),
+    "lbm_tau1_last_error": (ctypes.c_char_p, [_H]),
+    "lbm_tau1_launch_count": (_I64, [_H]),
+}
+
+_lib = None
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        self.status = status
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
+
+
+def load(build_if_missing: bool = False):
+    """Loads liblbm_tau1.so. Raises if it is missing (no CPU fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        if not build_if_missing:
+            raise RuntimeError(f"CUDA library {LIB_PATH} is not built; run paper_2312_14742_gb300.build")
+        _build.build()
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _fn(name):
+    return getattr(load(), name)
+
+
+# ---- the C entry points, same names -------------------------------------------------------
+
+def lbm_tau1_abi_version() -> int:
+    return _fn("lbm_tau1_abi_version")()
+
+
+def lbm_tau1_create(cfg: lbm_tau1_config) -> tuple[int, int | None]:
+    h = _H()
+    st = _fn("lbm_tau1_create")(ctypes.byref(cfg), ctypes.byref(h))
+    return st, h.value
+
+
+def lbm_tau1_set_geometry(h, solid_ptr, on_device: int) -> int:
+    return _fn("lbm_tau1_set_geometry")(h, solid_ptr, on_device)
+
+
+def lbm_tau1_set_fields(h, drho, ux, uy, uz, on_device: int) -> int:
+    return _fn("lbm_tau1_set_fields")(h, drho, ux, uy, uz, on_device)
+
+
+def lbm_tau1_get_fields(h, drho, ux, uy, uz, on_device: int) -> int:
+    return _fn("lbm_tau1_get_fields")(h, drho, ux, uy, uz, on_device)
+
+
+def lbm_tau1_step(h, nsteps: int) -> int:
+    return _fn("lbm_tau1_step")(h, nsteps)
+
+
+def lbm_tau1_reduce(h, stats: lbm_tau1_stats) -> int:
+    return _fn("lbm_tau1_reduce")(h, ctypes.byref(stats))
+
+
+def lbm_tau1_synchronize(h) -> int:
+    return _fn("lbm_tau1_synchronize")(h)
+
+
+def lbm_tau1_destroy(h) -> int:
+    return _fn("lbm_tau1_destroy")(h)
+
+
+def lbm_tau1_last_error(h) -> str:
+    s = _fn("lbm_tau1_last_error")(h)
+    return s.decode() if s else ""
+
+
+def lbm_tau1_launch_count(h) -> int:
+    return _fn("lbm_tau1_launch_count")(h)
+
+
+# ---- convenience owner of one handle ---------------------------------------------------------
+
+def _ptr(a, on_device: bool):
+    if a is None:
+        return None
+    if on_device:
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def _is_device(a) -> bool:
+    return hasattr(a, "is_cuda") and a.is_cuda
+
+
+class Tau1:
+    """One box: ``Tau1(q, (nx, ny, nz), storage="f32", periodic=(1,1,1), g=(gx,0,0))``."""
+
+    def __init__(self, q: int, dims, storage: str = "f32", periodic=(1, 1, 1), g=(0.0, 0.0, 0.0),
+                 kernel: str = "auto", stream=None, scheme: int = LBM_SCHEME_TAU1, layout: int = LBM_DENSE):
+        nx, ny, nz = (int(d) for d in dims)
+        cfg = lbm_tau1_config()
+        cfg.q, cfg.storage, cfg.layout, cfg.scheme = int(q), STORAGE[storage], int(layout), int(scheme)
+        cfg.nx, cfg.ny, cfg.nz = nx, ny, nz
+        for a in range(3):
+            cfg.periodic[a] = 1 if periodic[a] else 0
+            cfg.g[a] = float(g[a])
+        cfg.kernel = KERNELS[kernel]
+        cfg.cuda_stream = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+        st, h = lbm_tau1_create(cfg)
+        if st != LBM_OK:
+            raise LbmError(st, lbm_tau1_last_error(None))
+        self.h = h
+        self.dims = (nx, ny, nz)
+        self.shape = (nz, ny, nx)
+        self.q = int(q)
+        self.storage = storage
+        self.g = tuple(float(x) for x in g)
+
+    def _check(self, st: int) -> int:
+        if st != LBM_OK:
+            raise LbmError(st, lbm_tau1_last_error(self.h))
+        return st
+
+    def set_geometry(self, solid) -> None:
+        dev = _is_device(solid)
+        if not dev:
+            solid = np.ascontiguousarray(solid, dtype=np.uint8)
+        assert solid.numel() if dev else solid.size == self.dims[0] * self.dims[1] * self.dims[2]
+        self._keep = solid
+        self._check(lbm_tau1_set_geometry(self.h, _ptr(solid, dev), 1 if dev else 0))
+
+    def set_fields(self, drho, ux, uy, uz) -> None:
+        arrs = [drho, ux, uy, uz]
+        dev = _is_device(drho)
+        if not dev:
+            arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in arrs]
+        self._check(lbm_tau1_set_fields(self.h, *[_ptr(a, dev) for a in arrs], 1 if dev else 0))
+
+    def get_fields(self, out=None):
+        """Returns (drho, ux, uy, uz) as float64 numpy arrays (nz, ny, nx), or fills the
+        given torch CUDA tensors."""
+        if out is not None:
+            self._check(lbm_tau1_get_fields(self.h, *[_ptr(a, True) for a in out], 1))
+            return out
+        arrs = [np.empty(self.shape, dtype=np.float64) for _ in range(4)]
+        self._check(lbm_tau1_get_fields(self.h, *[_ptr(a, False) for a in arrs], 0))
+        return tuple(arrs)
+
+    def step(self, nsteps: int = 1) -> None:
+        self._check(lbm_tau1_step(self.h, int(nsteps)))
+
+    def reduce(self, allow_diverged: bool = False) -> dict:
+        s = lbm_tau1_stats()
+        st = lbm_tau1_reduce(self.h, s)
+        if st == LBM_EDIVERGED and allow_diverged:
+            d = s.as_dict()
+            d["diverged"] = True
+            return d
+        self._check(st)
+        return s.as_dict()
+
+    def synchronize(self) -> None:
+        self._check(lbm_tau1_synchronize(self.h))
+
+    @property
+    def launch_count(self) -> int:
+        return lbm_tau1_launch_count(self.h)
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            lbm_tau1_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
