@@ -156,6 +156,43 @@ const char* lbm_tau1_last_error(const lbm_tau1* h);
 /* Number of device kernel launches queued by this handle since creation. */
 int64_t lbm_tau1_launch_count(const lbm_tau1* h);
 
+/* ---- Reduction without allocation ------------------------------------------
+ * The paper has no counterpart to this entry point; it is a service for
+ * callers that cannot allocate device memory: code that works from a fixed
+ * device arena it manages itself, or inside a framework whose allocator must
+ * account for all device memory, and code that cannot afford the device-wide
+ * synchronisation cudaMalloc/cudaFree may cause. It runs the reduction of
+ * lbm_tau1_reduce on caller-owned arrays and calls no cudaMalloc, cudaFree
+ * or other allocating routine.
+ *
+ * Scratch: a static device array of LBM_TAU1_NOALLOC_MAX_BLOCKS rows of 8
+ * doubles (64 KiB) that every GPU loading this library holds until the
+ * process exits. All calls on a device share it; each call overwrites the
+ * rows it reads, so nothing carries over between calls. Calls whose work
+ * overlaps on the GPU (streams with no ordering between them) race on it.
+ * The first call on a device looks up the array's device address (with that
+ * device current) and caches it; make that first call before any stream
+ * capture.
+ *
+ * Arguments: storage (lbm_storage) and n = number of nodes; drho, ux, uy, uz
+ * = device arrays of n values in that storage format; inv_scale = host array
+ * of 4 floats (16-bit storage: value = stored * inv_scale; NULL = all 1);
+ * solid = device array of n bytes, bit 0 set = solid; g = host array of 3
+ * doubles (body force, for the physical velocity u + g/2); out = device
+ * array of 8 doubles receiving, in order: fluid count, sum drho, sum of the
+ * three physical velocity components, max |u + g/2|, non-finite count, 0
+ * (the raw sums behind lbm_tau1_stats). Work is queued on cuda_stream (NULL
+ * = legacy default stream) and the call returns without waiting.
+ * Errors: LBM_EINVAL (bad storage, NULL pointer, n < 1 or n larger than
+ * LBM_TAU1_NOALLOC_MAX_NODES), LBM_ECUDA. The message of the calling
+ * thread's last failure is in lbm_tau1_noalloc_last_error(). */
+#define LBM_TAU1_NOALLOC_MAX_BLOCKS 1024
+#define LBM_TAU1_NOALLOC_MAX_NODES (((int64_t)1) << 33)
+lbm_status lbm_tau1_reduce_noalloc(int32_t storage, int64_t n, const void* drho, const void* ux, const void* uy,
+                                   const void* uz, const float* inv_scale, const uint8_t* solid, const double* g,
+                                   double* out, void* cuda_stream);
+const char* lbm_tau1_noalloc_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

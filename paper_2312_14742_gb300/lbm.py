@@ -67,6 +67,8 @@ SIGNATURES = {
     "lbm_tau1_destroy": (_I, [_H]),
     "lbm_tau1_last_error": (ctypes.c_char_p, [_H]),
     "lbm_tau1_launch_count": (_I64, [_H]),
+    "lbm_tau1_reduce_noalloc": (_I, [ctypes.c_int32, _I64, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "lbm_tau1_noalloc_last_error": (ctypes.c_char_p, []),
 }
 
 _lib = None
@@ -147,6 +149,15 @@ def lbm_tau1_last_error(h) -> str:
 
 def lbm_tau1_launch_count(h) -> int:
     return _fn("lbm_tau1_launch_count")(h)
+
+
+def lbm_tau1_reduce_noalloc(storage, n, drho, ux, uy, uz, inv_scale, solid, g, out, stream) -> int:
+    return _fn("lbm_tau1_reduce_noalloc")(storage, n, drho, ux, uy, uz, inv_scale, solid, g, out, stream)
+
+
+def lbm_tau1_noalloc_last_error() -> str:
+    s = _fn("lbm_tau1_noalloc_last_error")()
+    return s.decode() if s else ""
 
 
 # ---- convenience owner of one handle ---------------------------------------------------------
