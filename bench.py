@@ -238,6 +238,8 @@ def run_ours(args):
     t = Tau1(args.q, (nx, ny, nz), storage=args.storage, periodic=(1, 1, 1), g=(args.gx, 0, 0),
              kernel=args.kernel, stream=stream)
     t.set_geometry(solid)
+    t.step(min(args.warmup, 50))
+    variant, tuned_ms = t.autotune(20)
     t.step(args.warmup)
     barrier()
 
@@ -303,7 +305,7 @@ def run_ours(args):
         "config": {"workload": workload_name(args, info), "n_nodes": n, "n_fluid": nf,
                    "l2": "inputs larger than L2 (two state copies + flags exceed 126 MB); no flush",
                    "parallelism": "replicas" if world > 1 else "single GPU", "reps": args.reps,
-                   "kernel": args.kernel},
+                   "kernel": args.kernel, "variant": variant, "autotune_ms": tuned_ms},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs",
                      "traffic": ncu_traffic(args),

@@ -70,8 +70,19 @@ typedef enum { LBM_DENSE = 0, LBM_SPARSE = 1 } lbm_layout;
  * LBM_F64 storage and the dense layout. */
 typedef enum { LBM_SCHEME_TAU1 = 0, LBM_SCHEME_BGK = 1 } lbm_scheme;
 
-/* Kernel choice for the dense Tau1 layout. AUTO picks the tiled kernel. */
-typedef enum { LBM_KERNEL_AUTO = 0, LBM_KERNEL_SIMPLE = 1, LBM_KERNEL_TILED = 2 } lbm_kernel;
+/* Kernel choice for the dense Tau1 layout. AUTO picks TILED when the box
+ * has fewer than 2^31 nodes, else SIMPLE. SIMPLE: one thread per node,
+ * neighbours from global memory. TILED: shared-memory exchange of each node's
+ * outgoing equilibria in a z-marching tile; for FP32/FP16/BF16 storage each
+ * thread advances two nodes in packed f32x2 lanes. TILED_SCALAR: the same
+ * tiled scheme with one node per thread (bitwise equal to TILED; kept as its
+ * cross-check). */
+typedef enum {
+    LBM_KERNEL_AUTO = 0,
+    LBM_KERNEL_SIMPLE = 1,
+    LBM_KERNEL_TILED = 2,
+    LBM_KERNEL_TILED_SCALAR = 3
+} lbm_kernel;
 
 typedef struct lbm_tau1_config {
     int32_t q;            /* lbm_lattice */
@@ -155,6 +166,24 @@ const char* lbm_tau1_last_error(const lbm_tau1* h);
 
 /* Number of device kernel launches queued by this handle since creation. */
 int64_t lbm_tau1_launch_count(const lbm_tau1* h);
+
+/* ---- Tile-shape autotuning (no counterpart in the paper, whose CPU kernels
+ * fix the chunk shape at compile time, Section 3.2). The tiled kernel comes in
+ * several tile-shape variants; the default is variant 0. */
+
+/* Number of variants of the handle's step kernel (1 if it has none). */
+int32_t lbm_tau1_variant_count(const lbm_tau1* h);
+
+/* Selects a variant, 0 <= variant < lbm_tau1_variant_count(h). LBM_EINVAL otherwise. */
+lbm_status lbm_tau1_set_variant(lbm_tau1* h, int32_t variant);
+
+/* Times every variant for `trials` step launches on the handle's current
+ * geometry and state (after one warm-up launch each), selects the fastest
+ * and returns its index in *chosen and its time per step in *ms_per_step
+ * (either may be NULL). The trial launches rewrite only the scratch copy, so
+ * the state and step counter are unchanged. Synchronises the stream.
+ * Errors: LBM_EINVAL (trials < 1), LBM_ESTATE (no geometry), LBM_ECUDA. */
+lbm_status lbm_tau1_autotune(lbm_tau1* h, int32_t trials, int32_t* chosen, float* ms_per_step);
 
 /* ---- Reduction without allocation ------------------------------------------
  * The paper has no counterpart to this entry point; it is a service for

@@ -20,8 +20,10 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "liblbm_tau1.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
-                     "-I", INCLUDE, "-I", CSRC]
+# -fmad=false: only the fma() calls written in the sources fuse, so every
+# kernel variant (one-node, two-node packed, simple) rounds the same way.
+NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC",
+                     "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
 
 
 def _nvcc() -> str:

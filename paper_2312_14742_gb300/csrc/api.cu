@@ -29,6 +29,7 @@ struct lbm_tau1 {
     float scale[4] = {1, 1, 1, 1};
     float inv_scale[4] = {1, 1, 1, 1};
     int kernel = LBM_KERNEL_SIMPLE;
+    int variant = 0;            // tile-shape variant of the tiled kernel
     int64_t launches = 0;
     std::string err;
 };
@@ -91,13 +92,16 @@ lbm_status check_ptr(lbm_tau1* h, const void* p, int on_device, const char* name
     return LBM_OK;
 }
 
-lbm_status launch_step(lbm_tau1* h)
+void fill_args(const lbm_tau1* h, StepArgs& a)
 {
-    StepArgs a;
     a.nx = h->cfg.nx;
     a.ny = h->cfg.ny;
     a.nz = h->cfg.nz;
-    for (int d = 0; d < 3; ++d) { a.periodic[d] = h->cfg.periodic[d] ? 1 : 0; a.g[d] = h->cfg.g[d]; }
+    for (int d = 0; d < 3; ++d) {
+        a.periodic[d] = h->cfg.periodic[d] ? 1 : 0;
+        a.g[d] = h->cfg.g[d];
+        a.gf[d] = (float)h->cfg.g[d];
+    }
     a.flags = h->flags;
     for (int f = 0; f < 4; ++f) {
         a.pre[f] = h->buf[h->cur][f];
@@ -105,9 +109,30 @@ lbm_status launch_step(lbm_tau1* h)
         a.inv_scale[f] = h->inv_scale[f];
         a.scale[f] = h->scale[f];
     }
+}
+
+int variant_count(const lbm_tau1* h)
+{
+    return (h->kernel == LBM_KERNEL_TILED && h->cfg.storage != LBM_F64) ? tau1_pair_variants(h->cfg.q) : 1;
+}
+
+cudaError_t launch_kernel(const lbm_tau1* h, int variant, const StepArgs& a)
+{
     cudaError_t e;
-    if (h->kernel == LBM_KERNEL_TILED) e = launch_tau1_tiled(h->cfg.q, h->cfg.storage, a, h->stream);
-    else e = launch_tau1_simple(h->cfg.q, h->cfg.storage, a, h->stream);
+    if (h->kernel == LBM_KERNEL_TILED && h->cfg.storage != LBM_F64)
+        e = launch_tau1_pair(h->cfg.q, h->cfg.storage, variant, a, h->stream);
+    else if (h->kernel == LBM_KERNEL_TILED || h->kernel == LBM_KERNEL_TILED_SCALAR)
+        e = launch_tau1_tiled(h->cfg.q, h->cfg.storage, a, h->stream);
+    else
+        e = launch_tau1_simple(h->cfg.q, h->cfg.storage, a, h->stream);
+    return e;
+}
+
+lbm_status launch_step(lbm_tau1* h)
+{
+    StepArgs a;
+    fill_args(h, a);
+    cudaError_t e = launch_kernel(h, h->variant, a);
     if (e != cudaSuccess) return cuda_fail(h, e, "tau1 step launch");
     ++h->launches;
     h->cur ^= 1;
@@ -134,7 +159,7 @@ lbm_status lbm_tau1_create(const lbm_tau1_config* cfg, lbm_tau1** out)
     if (cfg->nx < 1 || cfg->ny < 1 || cfg->nz < 1) return fail(nullptr, LBM_EINVAL, "create: box sizes must be >= 1");
     if (cfg->layout != LBM_DENSE) return fail(nullptr, LBM_EINVAL, "create: only the dense layout is available");
     if (cfg->scheme != LBM_SCHEME_TAU1) return fail(nullptr, LBM_EINVAL, "create: scheme not available");
-    if (cfg->kernel > LBM_KERNEL_TILED) return fail(nullptr, LBM_EINVAL, "create: bad kernel");
+    if (cfg->kernel > LBM_KERNEL_TILED_SCALAR) return fail(nullptr, LBM_EINVAL, "create: bad kernel");
     for (int d = 0; d < 3; ++d)
         if (!std::isfinite(cfg->g[d])) return fail(nullptr, LBM_EINVAL, "create: g must be finite");
     const int64_t n = (int64_t)cfg->nx * cfg->ny * cfg->nz;
@@ -147,9 +172,11 @@ lbm_status lbm_tau1_create(const lbm_tau1_config* cfg, lbm_tau1** out)
     h->n = n;
     h->elem = storage_bytes(cfg->storage);
     h->kernel = cfg->kernel;
-    if (h->kernel == LBM_KERNEL_AUTO)
-        h->kernel = tau1_tiled_supported(cfg->q, cfg->storage) ? LBM_KERNEL_TILED : LBM_KERNEL_SIMPLE;
-    if (h->kernel == LBM_KERNEL_TILED && !tau1_tiled_supported(cfg->q, cfg->storage)) {
+    const bool tiled_ok = cfg->storage == LBM_F64 ? tau1_tiled_supported(cfg->q, cfg->storage, n)
+                                                  : tau1_pair_supported(cfg->q, cfg->storage, n);
+    if (h->kernel == LBM_KERNEL_AUTO) h->kernel = tiled_ok ? LBM_KERNEL_TILED : LBM_KERNEL_SIMPLE;
+    if ((h->kernel == LBM_KERNEL_TILED && !tiled_ok) ||
+        (h->kernel == LBM_KERNEL_TILED_SCALAR && !tau1_tiled_supported(cfg->q, cfg->storage, n))) {
         delete h;
         return fail(nullptr, LBM_EINVAL, "create: tiled kernel not available for this lattice/storage");
     }
@@ -302,6 +329,56 @@ lbm_status lbm_tau1_step(lbm_tau1* h, int64_t nsteps)
     if (!h->has_geometry) return fail(h, LBM_ESTATE, "step: call set_geometry first");
     for (int64_t t = 0; t < nsteps; ++t)
         if (lbm_status st = launch_step(h)) return st;
+    return LBM_OK;
+}
+
+int32_t lbm_tau1_variant_count(const lbm_tau1* h) { return h ? variant_count(h) : 0; }
+
+lbm_status lbm_tau1_set_variant(lbm_tau1* h, int32_t variant)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "set_variant: NULL handle");
+    if (variant < 0 || variant >= variant_count(h)) return fail(h, LBM_EINVAL, "set_variant: no such variant");
+    h->variant = variant;
+    return LBM_OK;
+}
+
+lbm_status lbm_tau1_autotune(lbm_tau1* h, int32_t trials, int32_t* chosen, float* ms_per_step)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "autotune: NULL handle");
+    if (trials < 1) return fail(h, LBM_EINVAL, "autotune: trials < 1");
+    if (!h->has_geometry) return fail(h, LBM_ESTATE, "autotune: call set_geometry first");
+    // Every trial launch reads the current copy and rewrites the other one
+    // without swapping, so the state is left as it was.
+    StepArgs a;
+    fill_args(h, a);
+    cudaEvent_t e0, e1;
+    LBM_CUDA(h, cudaEventCreate(&e0), "autotune: event");
+    cudaError_t e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) { cudaEventDestroy(e0); return cuda_fail(h, e, "autotune: event"); }
+    const int nv = variant_count(h);
+    int best = h->variant;
+    float best_ms = 0.f;
+    for (int v = 0; v < nv && e == cudaSuccess; ++v) {
+        e = launch_kernel(h, v, a);  // warm-up (and first-use set-up)
+        ++h->launches;
+        if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+        for (int t = 0; t < trials && e == cudaSuccess; ++t) {
+            e = launch_kernel(h, v, a);
+            ++h->launches;
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        ms /= (float)trials;
+        if (e == cudaSuccess && (v == 0 || ms < best_ms)) { best = v; best_ms = ms; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(h, e, "autotune: trial");
+    h->variant = best;
+    if (chosen) *chosen = best;
+    if (ms_per_step) *ms_per_step = best_ms;
     return LBM_OK;
 }
 

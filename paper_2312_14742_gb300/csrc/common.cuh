@@ -26,14 +26,14 @@ template <> struct Storage<ST_F64> {
     using stype = double;
     using ctype = double;
     static constexpr int BYTES = 8;
-    __device__ static __forceinline__ double load(const stype* p, int64_t i, float) { return p[i]; }
+    __device__ static __forceinline__ double load(const stype* p, int64_t i, float) { return __ldg(p + i); }
     __device__ static __forceinline__ void store(stype* p, int64_t i, double v, float) { p[i] = v; }
 };
 template <> struct Storage<ST_F32> {
     using stype = float;
     using ctype = float;
     static constexpr int BYTES = 4;
-    __device__ static __forceinline__ float load(const stype* p, int64_t i, float) { return p[i]; }
+    __device__ static __forceinline__ float load(const stype* p, int64_t i, float) { return __ldg(p + i); }
     __device__ static __forceinline__ void store(stype* p, int64_t i, float v, float) { p[i] = v; }
 };
 template <> struct Storage<ST_F16S> {
@@ -42,7 +42,7 @@ template <> struct Storage<ST_F16S> {
     static constexpr int BYTES = 2;
     __device__ static __forceinline__ float load(const stype* p, int64_t i, float inv_scale)
     {
-        return __half2float(p[i]) * inv_scale;
+        return __half2float(__ldg(p + i)) * inv_scale;
     }
     __device__ static __forceinline__ void store(stype* p, int64_t i, float v, float scale)
     {
@@ -55,7 +55,7 @@ template <> struct Storage<ST_BF16S> {
     static constexpr int BYTES = 2;
     __device__ static __forceinline__ float load(const stype* p, int64_t i, float inv_scale)
     {
-        return __bfloat162float(p[i]) * inv_scale;
+        return __bfloat162float(__ldg(p + i)) * inv_scale;
     }
     __device__ static __forceinline__ void store(stype* p, int64_t i, float v, float scale)
     {
@@ -68,6 +68,7 @@ struct StepArgs {
     int nx, ny, nz;
     int periodic[3];
     double g[3];
+    float gf[3];          // g rounded to FP32 (for FP32 arithmetic)
     const uint8_t* flags;
     const void* pre[4];   // drho, ux, uy, uz (read)
     void* post[4];        // drho, ux, uy, uz (written on fluid nodes only)
@@ -75,8 +76,20 @@ struct StepArgs {
     float scale[4];       // 16-bit storage: stored = value * scale
 };
 
-// Correctly rounded reciprocal in the compute precision.
-__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+// Body force in the compute precision.
+template <typename T> __device__ __forceinline__ T gcomp(const StepArgs& a, int i);
+template <> __device__ __forceinline__ float gcomp<float>(const StepArgs& a, int i) { return a.gf[i]; }
+template <> __device__ __forceinline__ double gcomp<double>(const StepArgs& a, int i) { return a.g[i]; }
+
+// Reciprocal in the compute precision: FP64 correctly rounded; FP32 the
+// hardware approximation (rcp.approx, at most 1 ulp from the exact value),
+// used where rho = 1 + drho is near 1 and FP32 rounding dominates anyway.
+__device__ __forceinline__ float recip(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 __device__ __forceinline__ double recip(double x) { return __drcp_rn(x); }
 
 }  // namespace lbm

@@ -11,7 +11,11 @@ namespace lbm {
 // Tau1 step kernels (dense layout).
 cudaError_t launch_tau1_simple(int q, int storage, const StepArgs& a, cudaStream_t s);
 cudaError_t launch_tau1_tiled(int q, int storage, const StepArgs& a, cudaStream_t s);
-bool tau1_tiled_supported(int q, int storage);
+bool tau1_tiled_supported(int q, int storage, int64_t n);
+// Two-nodes-per-thread tiled kernel, packed f32x2 arithmetic (FP32/FP16/BF16 storage).
+cudaError_t launch_tau1_pair(int q, int storage, int variant, const StepArgs& a, cudaStream_t s);
+bool tau1_pair_supported(int q, int storage, int64_t n);
+int tau1_pair_variants(int q);
 
 // Geometry preparation: node flags from the solid mask.
 cudaError_t launch_build_flags(int q, int nx, int ny, int nz, const int periodic[3], const uint8_t* solid,

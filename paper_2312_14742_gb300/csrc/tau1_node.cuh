@@ -20,11 +20,14 @@ template <typename T> struct NodeMoments {
 template <typename T>
 __device__ __forceinline__ NodeMoments<T> node_moments(T drho, T ux, T uy, T uz, T gx, T gy, T gz)
 {
+    // Every fused multiply-add is written out, so that no kernel depends on
+    // the compiler's contraction choices (the packed two-node kernels and the
+    // scalar kernels then round identically).
     NodeMoments<T> m;
     const T rho = T(1) + drho;
     const T vx = ux + gx, vy = uy + gy, vz = uz + gz;
-    const T vv = vx * vx + vy * vy + vz * vz;
-    m.A = drho - T(1.5) * rho * vv;
+    const T vv = fma(vz, vz, fma(vy, vy, vx * vx));
+    m.A = fma(T(-1.5) * rho, vv, drho);
     const T r3 = T(3) * rho;
     m.Px = r3 * vx;
     m.Py = r3 * vy;

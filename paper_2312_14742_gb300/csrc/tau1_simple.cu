@@ -29,7 +29,7 @@ __global__ void __launch_bounds__(256) tau1_simple_kernel(StepArgs a)
     const st* pre1 = static_cast<const st*>(a.pre[1]);
     const st* pre2 = static_cast<const st*>(a.pre[2]);
     const st* pre3 = static_cast<const st*>(a.pre[3]);
-    const T gx = T(a.g[0]), gy = T(a.g[1]), gz = T(a.g[2]);
+    const T gx = gcomp<T>(a, 0), gy = gcomp<T>(a, 1), gz = gcomp<T>(a, 2);
 
     const NodeMoments<T> own = node_moments<T>(S::load(pre0, i, a.inv_scale[0]), S::load(pre1, i, a.inv_scale[1]),
                                                S::load(pre2, i, a.inv_scale[2]), S::load(pre3, i, a.inv_scale[3]),
@@ -38,7 +38,8 @@ __global__ void __launch_bounds__(256) tau1_simple_kernel(StepArgs a)
     acc.clear();
     acc.S[0] = own.A;  // rest direction: p = 0
 
-    static_for<1, Q>([&](auto kc) {
+    // one link: the equilibrium arriving along c_K
+    auto link = [&](auto kc) {
         constexpr int K = decltype(kc)::value;
         int sx = x - cvel(K, 0), sy = y - cvel(K, 1), sz = z - cvel(K, 2);
         bool wall = false;
@@ -62,7 +63,13 @@ __global__ void __launch_bounds__(256) tau1_simple_kernel(StepArgs a)
             f = feq_scaled(m.A, m.H, dir_dot<K, T>(m.Px, m.Py, m.Pz));
         }
         acc.template add<K>(f);
-    });
+    };
+    // Accumulation order: links with c_z = +1, then 0, then -1, each in k
+    // order (the order in which the z-marching kernels receive them), so all
+    // kernels give the same bits.
+    static_for<1, Q>([&](auto kc) { if constexpr (cvel(decltype(kc)::value, 2) == 1) link(kc); });
+    static_for<1, Q>([&](auto kc) { if constexpr (cvel(decltype(kc)::value, 2) == 0) link(kc); });
+    static_for<1, Q>([&](auto kc) { if constexpr (cvel(decltype(kc)::value, 2) == -1) link(kc); });
 
     T d, ux, uy, uz;
     node_finish<Q, T>(acc, d, ux, uy, uz);

@@ -25,8 +25,9 @@ LBM_F64, LBM_F32, LBM_F16S, LBM_BF16S = range(4)
 STORAGE = {"f64": LBM_F64, "f32": LBM_F32, "f16s": LBM_F16S, "bf16s": LBM_BF16S}
 LBM_DENSE, LBM_SPARSE = 0, 1
 LBM_SCHEME_TAU1, LBM_SCHEME_BGK = 0, 1
-LBM_KERNEL_AUTO, LBM_KERNEL_SIMPLE, LBM_KERNEL_TILED = 0, 1, 2
-KERNELS = {"auto": LBM_KERNEL_AUTO, "simple": LBM_KERNEL_SIMPLE, "tiled": LBM_KERNEL_TILED}
+LBM_KERNEL_AUTO, LBM_KERNEL_SIMPLE, LBM_KERNEL_TILED, LBM_KERNEL_TILED_SCALAR = 0, 1, 2, 3
+KERNELS = {"auto": LBM_KERNEL_AUTO, "simple": LBM_KERNEL_SIMPLE, "tiled": LBM_KERNEL_TILED,
+           "tiled_scalar": LBM_KERNEL_TILED_SCALAR}
 
 
 class lbm_tau1_config(ctypes.Structure):
@@ -67,6 +68,9 @@ SIGNATURES = {
     "lbm_tau1_destroy": (_I, [_H]),
     "lbm_tau1_last_error": (ctypes.c_char_p, [_H]),
     "lbm_tau1_launch_count": (_I64, [_H]),
+    "lbm_tau1_variant_count": (ctypes.c_int32, [_H]),
+    "lbm_tau1_set_variant": (_I, [_H, ctypes.c_int32]),
+    "lbm_tau1_autotune": (_I, [_H, ctypes.c_int32, _P, _P]),
     "lbm_tau1_reduce_noalloc": (_I, [ctypes.c_int32, _I64, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "lbm_tau1_noalloc_last_error": (ctypes.c_char_p, []),
 }
@@ -149,6 +153,18 @@ def lbm_tau1_last_error(h) -> str:
 
 def lbm_tau1_launch_count(h) -> int:
     return _fn("lbm_tau1_launch_count")(h)
+
+
+def lbm_tau1_variant_count(h) -> int:
+    return _fn("lbm_tau1_variant_count")(h)
+
+
+def lbm_tau1_set_variant(h, variant: int) -> int:
+    return _fn("lbm_tau1_set_variant")(h, variant)
+
+
+def lbm_tau1_autotune(h, trials: int, chosen=None, ms_per_step=None) -> int:
+    return _fn("lbm_tau1_autotune")(h, trials, chosen, ms_per_step)
 
 
 def lbm_tau1_reduce_noalloc(storage, n, drho, ux, uy, uz, inv_scale, solid, g, out, stream) -> int:
@@ -243,6 +259,20 @@ class Tau1:
 
     def synchronize(self) -> None:
         self._check(lbm_tau1_synchronize(self.h))
+
+    def autotune(self, trials: int = 20) -> tuple[int, float]:
+        """Times each tile-shape variant; keeps the fastest. Returns (variant, ms per step)."""
+        ch = ctypes.c_int32(0)
+        ms = ctypes.c_float(0)
+        self._check(lbm_tau1_autotune(self.h, int(trials), ctypes.byref(ch), ctypes.byref(ms)))
+        return ch.value, ms.value
+
+    def set_variant(self, v: int) -> None:
+        self._check(lbm_tau1_set_variant(self.h, int(v)))
+
+    @property
+    def variant_count(self) -> int:
+        return lbm_tau1_variant_count(self.h)
 
     @property
     def launch_count(self) -> int:

@@ -15,7 +15,7 @@ from paper_2312_14742_gb300 import Tau1, build
 
 pytestmark = pytest.mark.gpu
 
-KERNELS = ("simple", "tiled")
+KERNELS = ("simple", "tiled", "tiled_scalar")
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -228,3 +228,68 @@ def test_divergence_is_reported_not_trapped():
         assert d.get("diverged")
         t.step(3)
         t.synchronize()
+
+
+# ---------------------------------------------------------------------------
+# kernel cross-checks: the two-node packed kernel equals the one-node tiled
+# kernel bit for bit (same lane operations in the same order), in every
+# tile-shape variant; autotuning does not touch the state
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("q", (19, 27))
+@pytest.mark.parametrize("dims,per", [((64, 40, 33), (1, 1, 1)), ((45, 19, 21), (1, 0, 1)), ((7, 70, 9), (0, 1, 0))])
+def test_pair_kernel_bitwise_equals_scalar_tiled(q, dims, per):
+    """simple == tiled_scalar == tiled (every variant), bit for bit: the same
+    per-lane IEEE operations in the same order (only explicit fma fuse)."""
+    nx, ny, nz = dims
+    solid, _ = lbm_inputs.sphere_pack(nx, ny, nz, 3.0, 0.8, 4242 + nx)
+    st = lbm_inputs.random_fields(solid.shape, 17, 2e-3, 3e-3, solid)
+    g = (1e-5, 2e-6, -3e-6)
+    ref, _ = gpu_run(q, solid, per, g, "f32", 25, state=st, kernel="tiled_scalar")
+    simple, _ = gpu_run(q, solid, per, g, "f32", 25, state=st, kernel="simple")
+    for a in range(4):
+        assert np.array_equal(simple[a], ref[a]), ("simple", q, dims, a)
+    with Tau1(q, dims, storage="f32", periodic=per, g=g, kernel="tiled") as t:
+        nv = t.variant_count
+        assert nv >= 2
+    for v in range(nv):
+        with Tau1(q, dims, storage="f32", periodic=per, g=g, kernel="tiled") as t:
+            t.set_geometry(solid)
+            t.set_fields(*st)
+            t.set_variant(v)
+            t.step(25)
+            out = t.get_fields()
+        for a in range(4):
+            assert np.array_equal(out[a], ref[a]), (q, dims, v, a)
+
+
+@pytest.mark.parametrize("q", (19, 27))
+def test_fp64_simple_equals_tiled_bitwise(q):
+    solid, _ = lbm_inputs.sphere_pack(40, 24, 19, 3.0, 0.75, 31 + q)
+    st = lbm_inputs.random_fields(solid.shape, 32, 2e-3, 3e-3, solid)
+    g = (1e-5, -2e-6, 1e-6)
+    a, _ = gpu_run(q, solid, (1, 0, 1), g, "f64", 20, state=st, kernel="simple")
+    b, _ = gpu_run(q, solid, (1, 0, 1), g, "f64", 20, state=st, kernel="tiled")
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+def test_autotune_keeps_state():
+    solid, _ = lbm_inputs.sphere_pack(96, 64, 48, 5.0, 0.85, 77)
+    st = lbm_inputs.random_fields(solid.shape, 78, 1e-3, 1e-3, solid)
+    nz, ny, nx = solid.shape
+    with Tau1(19, (nx, ny, nz), storage="f32", g=(1e-5, 0, 0)) as t:
+        t.set_geometry(solid)
+        t.set_fields(*st)
+        t.step(3)
+        before = t.get_fields()
+        v, ms = t.autotune(5)
+        assert 0 <= v < t.variant_count and ms > 0
+        after = t.get_fields()
+        t.step(2)
+        a = t.get_fields()
+    for x, y in zip(before, after):
+        assert np.array_equal(x, y)
+    ref, _ = gpu_run(19, solid, (1, 1, 1), (1e-5, 0, 0), "f32", 5, state=st, kernel="tiled_scalar")
+    for x, y in zip(a, ref):
+        assert np.array_equal(x, y)
