@@ -73,16 +73,9 @@ typedef enum { LBM_SCHEME_TAU1 = 0, LBM_SCHEME_BGK = 1 } lbm_scheme;
 /* Kernel choice for the dense Tau1 layout. AUTO picks TILED when the box
  * has fewer than 2^31 nodes, else SIMPLE. SIMPLE: one thread per node,
  * neighbours from global memory. TILED: shared-memory exchange of each node's
- * outgoing equilibria in a z-marching tile; for FP32/FP16/BF16 storage each
- * thread advances two nodes in packed f32x2 lanes. TILED_SCALAR: the same
- * tiled scheme with one node per thread (bitwise equal to TILED; kept as its
- * cross-check). */
-typedef enum {
-    LBM_KERNEL_AUTO = 0,
-    LBM_KERNEL_SIMPLE = 1,
-    LBM_KERNEL_TILED = 2,
-    LBM_KERNEL_TILED_SCALAR = 3
-} lbm_kernel;
+ * outgoing equilibria in a z-marching tile, two nodes per thread (packed
+ * f32x2 lanes for FP32 arithmetic). Both give the same bits. */
+typedef enum { LBM_KERNEL_AUTO = 0, LBM_KERNEL_SIMPLE = 1, LBM_KERNEL_TILED = 2 } lbm_kernel;
 
 typedef struct lbm_tau1_config {
     int32_t q;            /* lbm_lattice */
@@ -114,9 +107,9 @@ typedef struct lbm_tau1 lbm_tau1;  /* opaque, owned by the library */
 /* ABI version of the loaded library (LBM_TAU1_ABI_VERSION it was built with). */
 int32_t lbm_tau1_abi_version(void);
 
-/* Validates cfg, allocates the device state of one box on cfg->cuda_stream
- * (two copies of drho, ux, uy, uz in the storage type, a uint8 node-flag
- * array, reduction scratch) and returns the handle in *out.
+/* Validates cfg, allocates the device state of one box (two copies of the
+ * state, one record {drho, ux, uy, uz} per node in the storage type; a
+ * uint8 node-flag array; reduction scratch) and returns the handle in *out.
  * Errors: LBM_EINVAL (bad cfg or NULL), LBM_ENOMEM, LBM_ECUDA. On error
  * *out is NULL and lbm_tau1_last_error(NULL) gives the message. */
 lbm_status lbm_tau1_create(const lbm_tau1_config* cfg, lbm_tau1** out);

@@ -16,8 +16,8 @@ struct lbm_tau1 {
     lbm_tau1_config cfg{};
     cudaStream_t stream = nullptr;
     int64_t n = 0;
-    size_t elem = 0;            // bytes per stored scalar
-    void* buf[2][4] = {};       // ping-pong copies of drho, ux, uy, uz
+    size_t node_bytes = 0;      // bytes per node record {drho, ux, uy, uz}
+    void* buf[2] = {};          // ping-pong copies of the state records
     int cur = 0;                // buf[cur] is the current (pre) state
     uint8_t* flags = nullptr;   // node flags
     double* red_partials = nullptr;
@@ -57,24 +57,14 @@ lbm_status cuda_fail(lbm_tau1* h, cudaError_t e, const char* what)
         if (e_ != cudaSuccess) return cuda_fail(h, e_, what); \
     } while (0)
 
-size_t storage_bytes(int st)
-{
-    switch (st) {
-    case LBM_F64: return 8;
-    case LBM_F32: return 4;
-    case LBM_F16S:
-    case LBM_BF16S: return 2;
-    default: return 0;
-    }
-}
+size_t storage_node_bytes(int st) { return (st >= LBM_F64 && st <= LBM_BF16S) ? (size_t)node_bytes(st) : 0; }
 
 void free_all(lbm_tau1* h)
 {
     if (!h) return;
     cudaStreamSynchronize(h->stream);
     for (int b = 0; b < 2; ++b)
-        for (int f = 0; f < 4; ++f)
-            if (h->buf[b][f]) cudaFree(h->buf[b][f]);
+        if (h->buf[b]) cudaFree(h->buf[b]);
     if (h->flags) cudaFree(h->flags);
     if (h->red_partials) cudaFree(h->red_partials);
     if (h->red_out) cudaFree(h->red_out);
@@ -102,10 +92,9 @@ void fill_args(const lbm_tau1* h, StepArgs& a)
         a.g[d] = h->cfg.g[d];
         a.gf[d] = (float)h->cfg.g[d];
     }
-    a.flags = h->flags;
+    a.pre = h->buf[h->cur];
+    a.post = h->buf[h->cur ^ 1];
     for (int f = 0; f < 4; ++f) {
-        a.pre[f] = h->buf[h->cur][f];
-        a.post[f] = h->buf[h->cur ^ 1][f];
         a.inv_scale[f] = h->inv_scale[f];
         a.scale[f] = h->scale[f];
     }
@@ -113,19 +102,13 @@ void fill_args(const lbm_tau1* h, StepArgs& a)
 
 int variant_count(const lbm_tau1* h)
 {
-    return (h->kernel == LBM_KERNEL_TILED && h->cfg.storage != LBM_F64) ? tau1_pair_variants(h->cfg.q) : 1;
+    return h->kernel == LBM_KERNEL_TILED ? tau1_tiled_variants(h->cfg.q, h->cfg.storage) : 1;
 }
 
 cudaError_t launch_kernel(const lbm_tau1* h, int variant, const StepArgs& a)
 {
-    cudaError_t e;
-    if (h->kernel == LBM_KERNEL_TILED && h->cfg.storage != LBM_F64)
-        e = launch_tau1_pair(h->cfg.q, h->cfg.storage, variant, a, h->stream);
-    else if (h->kernel == LBM_KERNEL_TILED || h->kernel == LBM_KERNEL_TILED_SCALAR)
-        e = launch_tau1_tiled(h->cfg.q, h->cfg.storage, a, h->stream);
-    else
-        e = launch_tau1_simple(h->cfg.q, h->cfg.storage, a, h->stream);
-    return e;
+    if (h->kernel == LBM_KERNEL_TILED) return launch_tau1_tiled(h->cfg.q, h->cfg.storage, variant, a, h->stream);
+    return launch_tau1_simple(h->cfg.q, h->cfg.storage, a, h->stream);
 }
 
 lbm_status launch_step(lbm_tau1* h)
@@ -155,11 +138,11 @@ lbm_status lbm_tau1_create(const lbm_tau1_config* cfg, lbm_tau1** out)
     if (out) *out = nullptr;
     if (!cfg || !out) return fail(nullptr, LBM_EINVAL, "create: NULL argument");
     if (cfg->q != 19 && cfg->q != 27) return fail(nullptr, LBM_EINVAL, "create: q must be 19 or 27");
-    if (storage_bytes(cfg->storage) == 0) return fail(nullptr, LBM_EINVAL, "create: bad storage");
+    if (storage_node_bytes(cfg->storage) == 0) return fail(nullptr, LBM_EINVAL, "create: bad storage");
     if (cfg->nx < 1 || cfg->ny < 1 || cfg->nz < 1) return fail(nullptr, LBM_EINVAL, "create: box sizes must be >= 1");
     if (cfg->layout != LBM_DENSE) return fail(nullptr, LBM_EINVAL, "create: only the dense layout is available");
     if (cfg->scheme != LBM_SCHEME_TAU1) return fail(nullptr, LBM_EINVAL, "create: scheme not available");
-    if (cfg->kernel > LBM_KERNEL_TILED_SCALAR) return fail(nullptr, LBM_EINVAL, "create: bad kernel");
+    if (cfg->kernel > LBM_KERNEL_TILED) return fail(nullptr, LBM_EINVAL, "create: bad kernel");
     for (int d = 0; d < 3; ++d)
         if (!std::isfinite(cfg->g[d])) return fail(nullptr, LBM_EINVAL, "create: g must be finite");
     const int64_t n = (int64_t)cfg->nx * cfg->ny * cfg->nz;
@@ -170,19 +153,16 @@ lbm_status lbm_tau1_create(const lbm_tau1_config* cfg, lbm_tau1** out)
     h->cfg = *cfg;
     h->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
     h->n = n;
-    h->elem = storage_bytes(cfg->storage);
+    h->node_bytes = storage_node_bytes(cfg->storage);
     h->kernel = cfg->kernel;
-    const bool tiled_ok = cfg->storage == LBM_F64 ? tau1_tiled_supported(cfg->q, cfg->storage, n)
-                                                  : tau1_pair_supported(cfg->q, cfg->storage, n);
+    const bool tiled_ok = tau1_tiled_supported(cfg->q, cfg->storage, n);
     if (h->kernel == LBM_KERNEL_AUTO) h->kernel = tiled_ok ? LBM_KERNEL_TILED : LBM_KERNEL_SIMPLE;
-    if ((h->kernel == LBM_KERNEL_TILED && !tiled_ok) ||
-        (h->kernel == LBM_KERNEL_TILED_SCALAR && !tau1_tiled_supported(cfg->q, cfg->storage, n))) {
+    if (h->kernel == LBM_KERNEL_TILED && !tiled_ok) {
         delete h;
         return fail(nullptr, LBM_EINVAL, "create: tiled kernel not available for this lattice/storage");
     }
     cudaError_t e = cudaSuccess;
-    for (int b = 0; b < 2 && e == cudaSuccess; ++b)
-        for (int f = 0; f < 4 && e == cudaSuccess; ++f) e = cudaMalloc(&h->buf[b][f], (size_t)n * h->elem);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaMalloc(&h->buf[b], (size_t)n * h->node_bytes);
     if (e == cudaSuccess) e = cudaMalloc(&h->flags, (size_t)n);
     if (e == cudaSuccess) e = cudaMalloc(&h->red_partials, (size_t)reduce_blocks(n) * RED_FIELDS * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&h->red_out, RED_FIELDS * sizeof(double));
@@ -229,10 +209,13 @@ lbm_status lbm_tau1_set_geometry(lbm_tau1* h, const uint8_t* solid, int on_devic
     ++h->launches;
     if (tmp) cudaFreeAsync(tmp, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "set_geometry: flags kernel");
-    for (int b = 0; b < 2; ++b)
-        for (int f = 0; f < 4; ++f)
-            LBM_CUDA(h, cudaMemsetAsync(h->buf[b][f], 0, (size_t)h->n * h->elem, h->stream), "set_geometry: clear");
     for (int f = 0; f < 4; ++f) h->scale[f] = h->inv_scale[f] = 1.0f;
+    for (int b = 0; b < 2; ++b) {
+        // drho = 0, u = 0 on fluid nodes; solid nodes marked with drho = NaN
+        e = launch_import_state(h->cfg.storage, h->n, nullptr, h->buf[b], h->flags, h->scale, h->stream);
+        ++h->launches;
+        if (e != cudaSuccess) return cuda_fail(h, e, "set_geometry: state init");
+    }
     h->cur = 0;
     h->step = 0;
     h->n_fluid = -1;
@@ -283,9 +266,7 @@ lbm_status lbm_tau1_set_fields(lbm_tau1* h, const double* drho, const double* ux
             h->inv_scale[f] = std::ldexp(1.0f, -ex);
         }
     }
-    void* dst[4];
-    for (int f = 0; f < 4; ++f) dst[f] = h->buf[h->cur][f];
-    cudaError_t e = launch_import_fields(h->cfg.storage, h->n, dsrc, dst, h->flags, h->scale, h->stream);
+    cudaError_t e = launch_import_state(h->cfg.storage, h->n, dsrc, h->buf[h->cur], h->flags, h->scale, h->stream);
     ++h->launches;
     if (tmp) cudaFreeAsync(tmp, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "set_fields: import kernel");
@@ -305,9 +286,7 @@ lbm_status lbm_tau1_get_fields(lbm_tau1* h, double* drho, double* ux, double* uy
     LBM_CUDA(h, cudaMallocAsync((void**)&tmp, 4 * bytes, h->stream), "get_fields: staging allocation");
     double* ddst[4];
     for (int f = 0; f < 4; ++f) ddst[f] = (on_device && dst[f]) ? dst[f] : tmp + f * h->n;
-    const void* src[4];
-    for (int f = 0; f < 4; ++f) src[f] = h->buf[h->cur][f];
-    cudaError_t e = launch_export_fields(h->cfg.storage, h->n, src, ddst, h->inv_scale, h->stream);
+    cudaError_t e = launch_export_state(h->cfg.storage, h->n, h->buf[h->cur], ddst, h->flags, h->inv_scale, h->stream);
     ++h->launches;
     if (e != cudaSuccess) { cudaFreeAsync(tmp, h->stream); return cuda_fail(h, e, "get_fields: export kernel"); }
     if (!on_device) {
@@ -387,9 +366,8 @@ lbm_status lbm_tau1_reduce(lbm_tau1* h, lbm_tau1_stats* out)
     if (!h) return fail(nullptr, LBM_EINVAL, "reduce: NULL handle");
     if (!out) return fail(h, LBM_EINVAL, "reduce: NULL output");
     if (!h->has_geometry) return fail(h, LBM_ESTATE, "reduce: call set_geometry first");
-    const void* f[4];
-    for (int a = 0; a < 4; ++a) f[a] = h->buf[h->cur][a];
-    cudaError_t e = launch_reduce(h->cfg.storage, h->n, f, h->inv_scale, h->flags, h->cfg.g, h->red_partials,
+    const void* f[4] = {h->buf[h->cur], nullptr, nullptr, nullptr};
+    cudaError_t e = launch_reduce(h->cfg.storage, true, h->n, f, h->inv_scale, h->flags, h->cfg.g, h->red_partials,
                                   h->red_out, h->stream);
     h->launches += 2;
     if (e != cudaSuccess) return cuda_fail(h, e, "reduce: kernel");

@@ -54,69 +54,74 @@ cudaError_t launch_build_flags(int q, int nx, int ny, int nz, const int periodic
 struct F64x4 {
     const double* p[4];
 };
-struct OutX4 {
-    void* p[4];
+struct D64x4 {
+    double* p[4];
 };
 struct Sc4 {
     float v[4];
 };
 
 template <int ST>
-__global__ void import_kernel(int64_t n, F64x4 src, OutX4 dst, const uint8_t* __restrict__ flags, Sc4 scale)
+__global__ void import_kernel(int64_t n, F64x4 src, void* dst, const uint8_t* __restrict__ flags, Sc4 scale)
 {
     using S = Storage<ST>;
-    using st = typename S::stype;
     using T = typename S::ctype;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const bool solid = flags[i] & FLAG_SOLID;
+        T v[4] = {T(0), T(0), T(0), T(0)};
+        if (flags[i] & FLAG_SOLID) {
+            v[0] = T(NAN);
+        } else if (src.p[0]) {
 #pragma unroll
-        for (int f = 0; f < 4; ++f)
-            S::store(static_cast<st*>(dst.p[f]), i, solid ? T(0) : T(src.p[f][i]), scale.v[f]);
+            for (int f = 0; f < 4; ++f) v[f] = T(src.p[f][i]);
+        }
+        S::store(dst, (uint32_t)i, v[0], v[1], v[2], v[3], scale.v);
     }
 }
 
 template <int ST>
-__global__ void export_kernel(int64_t n, OutX4 src, OutX4 dst, Sc4 inv_scale)
+__global__ void export_kernel(int64_t n, const void* src, D64x4 dst, const uint8_t* __restrict__ flags, Sc4 inv)
 {
     using S = Storage<ST>;
-    using st = typename S::stype;
+    using T = typename S::ctype;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        T v[4];
+        S::load(src, (uint32_t)i, inv.v, v[0], v[1], v[2], v[3]);
+        const bool solid = flags[i] & FLAG_SOLID;
 #pragma unroll
         for (int f = 0; f < 4; ++f)
-            static_cast<double*>(dst.p[f])[i] = (double)S::load(static_cast<const st*>(src.p[f]), i, inv_scale.v[f]);
+            if (dst.p[f]) dst.p[f][i] = solid ? 0.0 : (double)v[f];
     }
 }
 
-cudaError_t launch_import_fields(int storage, int64_t n, const double* const src[4], void* const dst[4],
-                                 const uint8_t* flags, const float scale[4], cudaStream_t s)
+cudaError_t launch_import_state(int storage, int64_t n, const double* const src[4], void* dst, const uint8_t* flags,
+                                const float scale[4], cudaStream_t s)
 {
     F64x4 a;
-    OutX4 b;
     Sc4 c;
-    for (int f = 0; f < 4; ++f) { a.p[f] = src[f]; b.p[f] = dst[f]; c.v[f] = scale[f]; }
+    for (int f = 0; f < 4; ++f) { a.p[f] = src ? src[f] : nullptr; c.v[f] = scale[f]; }
     const unsigned g = grid_for(n, 256);
     switch (storage) {
-    case ST_F64: import_kernel<ST_F64><<<g, 256, 0, s>>>(n, a, b, flags, c); break;
-    case ST_F32: import_kernel<ST_F32><<<g, 256, 0, s>>>(n, a, b, flags, c); break;
-    case ST_F16S: import_kernel<ST_F16S><<<g, 256, 0, s>>>(n, a, b, flags, c); break;
-    case ST_BF16S: import_kernel<ST_BF16S><<<g, 256, 0, s>>>(n, a, b, flags, c); break;
+    case ST_F64: import_kernel<ST_F64><<<g, 256, 0, s>>>(n, a, dst, flags, c); break;
+    case ST_F32: import_kernel<ST_F32><<<g, 256, 0, s>>>(n, a, dst, flags, c); break;
+    case ST_F16S: import_kernel<ST_F16S><<<g, 256, 0, s>>>(n, a, dst, flags, c); break;
+    case ST_BF16S: import_kernel<ST_BF16S><<<g, 256, 0, s>>>(n, a, dst, flags, c); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_export_fields(int storage, int64_t n, const void* const src[4], double* const dst[4],
-                                 const float inv_scale[4], cudaStream_t s)
+cudaError_t launch_export_state(int storage, int64_t n, const void* src, double* const dst[4], const uint8_t* flags,
+                                const float inv_scale[4], cudaStream_t s)
 {
-    OutX4 a, b;
+    D64x4 b;
     Sc4 c;
-    for (int f = 0; f < 4; ++f) { a.p[f] = const_cast<void*>(src[f]); b.p[f] = dst[f]; c.v[f] = inv_scale[f]; }
+    for (int f = 0; f < 4; ++f) { b.p[f] = dst[f]; c.v[f] = inv_scale[f]; }
     const unsigned g = grid_for(n, 256);
     switch (storage) {
-    case ST_F64: export_kernel<ST_F64><<<g, 256, 0, s>>>(n, a, b, c); break;
-    case ST_F32: export_kernel<ST_F32><<<g, 256, 0, s>>>(n, a, b, c); break;
-    case ST_F16S: export_kernel<ST_F16S><<<g, 256, 0, s>>>(n, a, b, c); break;
-    case ST_BF16S: export_kernel<ST_BF16S><<<g, 256, 0, s>>>(n, a, b, c); break;
+    case ST_F64: export_kernel<ST_F64><<<g, 256, 0, s>>>(n, src, b, flags, c); break;
+    case ST_F32: export_kernel<ST_F32><<<g, 256, 0, s>>>(n, src, b, flags, c); break;
+    case ST_F16S: export_kernel<ST_F16S><<<g, 256, 0, s>>>(n, src, b, flags, c); break;
+    case ST_BF16S: export_kernel<ST_BF16S><<<g, 256, 0, s>>>(n, src, b, flags, c); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -64,12 +64,27 @@ __device__ __forceinline__ void block_reduce(double* v, double (*sm)[RT])
     }
 }
 
-template <int ST>
+// One field value of node i from an array of one field (plain storage
+// element type of the format).
+template <int ST> struct Plain;
+template <> struct Plain<ST_F64> { __device__ static double get(const void* p, int64_t i, float) { return static_cast<const double*>(p)[i]; } };
+template <> struct Plain<ST_F32> { __device__ static double get(const void* p, int64_t i, float) { return static_cast<const float*>(p)[i]; } };
+template <> struct Plain<ST_F16S> {
+    __device__ static double get(const void* p, int64_t i, float inv) { return __half2float(static_cast<const __half*>(p)[i]) * inv; }
+};
+template <> struct Plain<ST_BF16S> {
+    __device__ static double get(const void* p, int64_t i, float inv)
+    {
+        return __bfloat162float(static_cast<const __nv_bfloat16*>(p)[i]) * inv;
+    }
+};
+
+template <int ST, bool AOS>
 __global__ void __launch_bounds__(RT) reduce_pass1(int64_t n, Fields4 fl, Sc4r inv, const uint8_t* __restrict__ flags,
                                                    double hgx, double hgy, double hgz, double* __restrict__ partials)
 {
     using S = Storage<ST>;
-    using st = typename S::stype;
+    using T = typename S::ctype;
     __shared__ double sm[RED_FIELDS][RT];
     const int64_t per = (n + gridDim.x - 1) / gridDim.x;
     const int64_t lo = (int64_t)blockIdx.x * per;
@@ -77,10 +92,20 @@ __global__ void __launch_bounds__(RT) reduce_pass1(int64_t n, Fields4 fl, Sc4r i
     double v[RED_FIELDS] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int64_t i = lo + threadIdx.x; i < hi; i += RT) {
         if (flags[i] & FLAG_SOLID) continue;
-        const double d = (double)S::load(static_cast<const st*>(fl.p[0]), i, inv.v[0]);
-        const double px = (double)S::load(static_cast<const st*>(fl.p[1]), i, inv.v[1]) + hgx;
-        const double py = (double)S::load(static_cast<const st*>(fl.p[2]), i, inv.v[2]) + hgy;
-        const double pz = (double)S::load(static_cast<const st*>(fl.p[3]), i, inv.v[3]) + hgz;
+        double d, px, py, pz;
+        if constexpr (AOS) {
+            T v0, v1, v2, v3;
+            S::load(fl.p[0], (uint32_t)i, inv.v, v0, v1, v2, v3);
+            d = (double)v0;
+            px = (double)v1 + hgx;
+            py = (double)v2 + hgy;
+            pz = (double)v3 + hgz;
+        } else {
+            d = Plain<ST>::get(fl.p[0], i, inv.v[0]);
+            px = Plain<ST>::get(fl.p[1], i, inv.v[1]) + hgx;
+            py = Plain<ST>::get(fl.p[2], i, inv.v[2]) + hgy;
+            pz = Plain<ST>::get(fl.p[3], i, inv.v[3]) + hgz;
+        }
         v[RED_NFLUID] += 1.0;
         v[RED_DRHO] += d;
         v[RED_PX] += px;
@@ -107,7 +132,7 @@ __global__ void __launch_bounds__(RT) reduce_pass2(int blocks, const double* __r
         for (int f = 0; f < RED_FIELDS; ++f) out[f] = v[f];
 }
 
-cudaError_t launch_reduce(int storage, int64_t n, const void* const fields[4], const float inv_scale[4],
+cudaError_t launch_reduce(int storage, bool aos, int64_t n, const void* const fields[4], const float inv_scale[4],
                           const uint8_t* flags, const double g[3], double* partials, double* out, cudaStream_t s)
 {
     Fields4 f;
@@ -115,11 +140,15 @@ cudaError_t launch_reduce(int storage, int64_t n, const void* const fields[4], c
     for (int a = 0; a < 4; ++a) { f.p[a] = fields[a]; sc.v[a] = inv_scale[a]; }
     const int blocks = reduce_blocks(n);
     const double hx = 0.5 * g[0], hy = 0.5 * g[1], hz = 0.5 * g[2];
-    switch (storage) {
-    case ST_F64: reduce_pass1<ST_F64><<<blocks, RT, 0, s>>>(n, f, sc, flags, hx, hy, hz, partials); break;
-    case ST_F32: reduce_pass1<ST_F32><<<blocks, RT, 0, s>>>(n, f, sc, flags, hx, hy, hz, partials); break;
-    case ST_F16S: reduce_pass1<ST_F16S><<<blocks, RT, 0, s>>>(n, f, sc, flags, hx, hy, hz, partials); break;
-    case ST_BF16S: reduce_pass1<ST_BF16S><<<blocks, RT, 0, s>>>(n, f, sc, flags, hx, hy, hz, partials); break;
+    switch (storage * 2 + (aos ? 1 : 0)) {
+    case 2 * ST_F64: reduce_pass1<ST_F64, false><<<blocks, RT, 0, s>>>(n, f, sc, flags, hx, hy, hz, partials); break;
+    case 2 * ST_F64 + 1: reduce_pass1<ST_F64, true><<<blocks, RT, 0, s>>>(n, f, sc, flags, hx, hy, hz, partials); break;
+    case 2 * ST_F32: reduce_pass1<ST_F32, false><<<blocks, RT, 0, s>>>(n, f, sc, flags, hx, hy, hz, partials); break;
+    case 2 * ST_F32 + 1: reduce_pass1<ST_F32, true><<<blocks, RT, 0, s>>>(n, f, sc, flags, hx, hy, hz, partials); break;
+    case 2 * ST_F16S: reduce_pass1<ST_F16S, false><<<blocks, RT, 0, s>>>(n, f, sc, flags, hx, hy, hz, partials); break;
+    case 2 * ST_F16S + 1: reduce_pass1<ST_F16S, true><<<blocks, RT, 0, s>>>(n, f, sc, flags, hx, hy, hz, partials); break;
+    case 2 * ST_BF16S: reduce_pass1<ST_BF16S, false><<<blocks, RT, 0, s>>>(n, f, sc, flags, hx, hy, hz, partials); break;
+    case 2 * ST_BF16S + 1: reduce_pass1<ST_BF16S, true><<<blocks, RT, 0, s>>>(n, f, sc, flags, hx, hy, hz, partials); break;
     default: return cudaErrorInvalidValue;
     }
     cudaError_t e = cudaGetLastError();

@@ -88,7 +88,7 @@ lbm_status lbm_tau1_reduce_noalloc(int32_t storage, int64_t n, const void* drho,
     if (lbm_status st = scratch_address(&partials)) return st;
     const float one[4] = {1.f, 1.f, 1.f, 1.f};
     const void* fields[4] = {drho, ux, uy, uz};
-    cudaError_t e = launch_reduce(storage, n, fields, inv_scale ? inv_scale : one, solid, g,
+    cudaError_t e = launch_reduce(storage, false, n, fields, inv_scale ? inv_scale : one, solid, g,
                                   static_cast<double*>(partials), out, static_cast<cudaStream_t>(cuda_stream));
     if (e != cudaSuccess) return noalloc_fail(LBM_ECUDA, "kernel launch", e);
     return LBM_OK;

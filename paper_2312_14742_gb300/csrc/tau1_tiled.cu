@@ -1,37 +1,43 @@
 // Tiled Tau1 step kernel: 2.5D z-march with shared-memory exchange of the
-// equilibria each node sends to its in-plane neighbours.
+// equilibria each node sends to its in-plane neighbours; every thread updates
+// two nodes in the lanes of a two-lane type (packed f32x2 for FP32
+// arithmetic, two FP64 lanes for FP64).
 //
 // Tau1 (Eq. LBMTau1) says the population arriving at x along c_k is
 // f_k^eq of the source x - c_k. Each node therefore evaluates its q outgoing
-// equilibria once (Eq. feq, scaled by 1/w_k, as pairs k / inv(k) that share
+// equilibria once (Eq. feq scaled by 1/w_k, in pairs k / inv(k) that share
 // one fma chain) and every destination only gathers and adds. This is the
 // buffering of neighbour data inside the processor that the paper's
 // complexity analysis (Section 2.1.3) asks for, so that HBM sees one read and
-// one write of (rho, u) per node.
+// one write of (rho, u) per node. The velocity is multiplied once by 1/rho
+// (Algorithm "Optimized Tau1 ... stores velocity").
 //
-// Block = TX x TY threads = one tile of an x-y plane (a warp is one tile row)
-// marching over planes z0..z1-1. At the "arrival" of plane p every tile
-// position computes its outgoing values; for each in-plane direction
-// (dx, dy) != 0 it stores the 4-vector {c_z = -1, 0, +1, unused} in slot
-// p % 2 of shared memory (D3Q19's four in-plane diagonals, which only exist
-// with c_z = 0, go to four scalar arrays instead). The one-node ring around
-// the tile exports only the directions that point into the tile. After one
-// barrier each thread gathers from its 8 in-plane neighbours: the c_z = -1
-// components complete destination plane p-1, c_z = 0 components go into
-// plane p, and c_z = +1 components wait one arrival in registers. The
-// (0,0,+-1) links and the rest direction never leave the thread.
+// Tile = 32 x 2H nodes, block = 32 x H threads; a thread owns the nodes
+// (x, y) [lane A] and (x, y + H) [lane B] of the tile and marches in z.
+// Shared memory is indexed by "pair positions" (x', y'), x' in [-1, 32],
+// y' in [-1, H], lane A = tile node (x', y'), lane B = node (x', y' + H), so
+// that both sources x - c_k of a thread sit at one pair position
+// (x - c_x, y - c_y). Pair row -1 holds the halo row below (A) and interior
+// row H-1 (B); pair row H holds interior row H (A) and the halo row above
+// (B). Warp 0 computes both halo rows as one two-lane pair, warp 1 the two
+// halo columns; the owners of rows H-1 and H copy their exports into pair
+// rows -1 and H. Halo nodes export only the directions pointing into the tile.
 //
-// Walls (Algorithm "Complete Tau1 ... halfway bounce-back"): a solid node, or
-// a position beyond a non-periodic face, exports a NaN payload (MARKER) that
-// arithmetic never produces. For a warp that holds a node with a wall link,
-// each MARKER is replaced by the node's own outgoing value in direction
-// inv(k) of the destination plane: for plane p it is in registers; for the
-// c_z = -1 links of plane p-1 the needed own values (directions (., ., +1))
-// were kept from the previous arrival. Other warps add without checks.
+// At the "arrival" of plane p every position stores, per in-plane direction
+// (dx, dy) != 0, its values for c_z = -1, 0, +1 and its solid fraction
+// sigma (1 for a solid node or a position beyond a non-periodic face, else
+// 0). Solid nodes export 0. After one barrier each thread gathers: c_z = -1
+// values complete destination plane p - 1, c_z = 0 values go into plane p,
+// c_z = +1 values wait one arrival in registers; (0,0,+-1) and rest never
+// leave the thread. Walls (Algorithm "Complete Tau1 ... halfway
+// bounce-back") enter every link as fma(sigma, b, v), where v is the
+// gathered value and b the destination node's own outgoing value in
+// direction inv(k): v for a fluid source, b for a wall, with no branch.
 //
 // Grid: one block per (z-chunk, tile), ordered chunk-major, so the tiles of a
-// chunk run side by side and each tile's halo reads hit L2.
+// chunk run side by side and halo reads hit L2.
 #include "kernels.h"
+#include "pack2.cuh"
 #include "static_for.cuh"
 #include "tau1_node.cuh"
 
@@ -39,23 +45,6 @@ namespace lbm {
 
 namespace {
 
-template <typename T> struct __align__(4 * sizeof(T)) V4 {
-    T x, y, z, w;
-};
-
-template <typename T> struct Marker;
-template <> struct Marker<float> {
-    static constexpr unsigned BITS = 0x7FBADBADu;
-    __device__ static __forceinline__ float value() { return __uint_as_float(BITS); }
-    __device__ static __forceinline__ bool is(float v) { return __float_as_uint(v) == BITS; }
-};
-template <> struct Marker<double> {
-    static constexpr unsigned long long BITS = 0x7FF4BADBADBADBADull;
-    __device__ static __forceinline__ double value() { return __longlong_as_double((long long)BITS); }
-    __device__ static __forceinline__ bool is(double v) { return (unsigned long long)__double_as_longlong(v) == BITS; }
-};
-
-// Direction index of velocity (cx, cy, cz), or -1.
 __host__ __device__ constexpr int kdir(int cx, int cy, int cz)
 {
     for (int k = 0; k < 27; ++k)
@@ -63,9 +52,8 @@ __host__ __device__ constexpr int kdir(int cx, int cy, int cz)
     return -1;
 }
 
-// Exchange layout. Block b carries in-plane direction (dx(b), dy(b)) with
-// lanes c_z = -1, 0, +1. D3Q19 has 4 face blocks plus 4 diagonal scalars
-// (diagonal j = in-plane direction (ddx(j), ddy(j)), c_z = 0).
+// Exchange blocks (in-plane direction of block b) and D3Q19 diagonal slots
+// (in-plane diagonal j, c_z = 0 only).
 template <int Q> struct Xch;
 template <> struct Xch<19> {
     static constexpr int NB = 4, ND = 4;
@@ -87,32 +75,34 @@ template <> struct Xch<27> {
     __host__ __device__ static constexpr int ddx(int) { return 0; }
     __host__ __device__ static constexpr int ddy(int) { return 0; }
 };
+__host__ __device__ constexpr int block_of(int dx, int dy)
+{
+    return dy == 0 ? (dx > 0 ? 0 : 1) : (dx == 0 ? (dy > 0 ? 2 : 3) : (dx == dy ? (dx > 0 ? 4 : 5) : (dx > 0 ? 6 : 7)));
+}
+__host__ __device__ constexpr int diag_of(int dx, int dy) { return dx == dy ? (dx > 0 ? 0 : 1) : (dx > 0 ? 3 : 2); }
 
-// Raw state of one node as loaded from global memory.
-template <typename T> struct Raw {
-    T d, ux, uy, uz;
-    int flag;  // node flags; FLAG_SOLID also for positions beyond a non-periodic face
-};
+template <typename E> struct __align__(4 * sizeof(E)) V4 { E x, y, z, w; };
+template <typename E> struct __align__(2 * sizeof(E)) V2 { E x, y; };
 
-template <int Q, int ST, int TX, int TY> struct Cfg {
-    using S = Storage<ST>;
-    using T = typename S::ctype;
-    using st = typename S::stype;
+template <int Q, int TX, int H, typename E> struct TCfg {
     static constexpr int NB = Xch<Q>::NB, ND = Xch<Q>::ND;
     static constexpr int PW = TX + 2;
-    static constexpr int NPOS = (TX + 2) * (TY + 2);
-    static constexpr int NHALO = 2 * TX + 2 * (TY + 2);
-    static constexpr int NT = TX * TY;
-    static constexpr int NSLOT = 2;
-    static constexpr size_t SLOT_BYTES = (size_t)NPOS * (NB * sizeof(V4<T>) + ND * sizeof(T));
-    static constexpr size_t SMEM = NSLOT * SLOT_BYTES;
-    static_assert(NHALO <= NT, "the halo ring must fit one position per thread");
+    static constexpr int NPP = (TX + 2) * (H + 2);  // pair positions
+    static constexpr int NT = TX * H;
+    // slot: L01[NB][NPP] {c_z=-1: A, B; c_z=0: A, B} | L2[NB][NPP] {c_z=+1: A, B}
+    //       | DG[ND][NPP] {A, B} | SG[NPP] {sigma A, sigma B}
+    static constexpr size_t L01_BYTES = (size_t)NB * NPP * sizeof(V4<E>);
+    static constexpr size_t L2_BYTES = (size_t)NB * NPP * sizeof(V2<E>);
+    static constexpr size_t DG_BYTES = (size_t)ND * NPP * sizeof(V2<E>);
+    static constexpr size_t SG_BYTES = (size_t)NPP * sizeof(V2<E>);
+    static constexpr size_t SLOT_BYTES = L01_BYTES + L2_BYTES + DG_BYTES + SG_BYTES;
+    static constexpr size_t SMEM = 2 * SLOT_BYTES;
     static_assert(TX == 32, "a warp is one tile row");
+    static_assert(H >= 2 && 2 * (H + 2) <= 32, "warp 1 holds both halo columns");
 };
 
-__device__ __forceinline__ int pos_of(int tx, int ty, int pw) { return (ty + 1) * pw + (tx + 1); }
+__device__ __forceinline__ int ppos(int tx, int ty, int pw) { return (ty + 1) * pw + (tx + 1); }
 
-// Wraps c on a periodic axis; false if it lies beyond a non-periodic face.
 __device__ __forceinline__ bool wrap_coord(int& c, int n, int periodic)
 {
     if (c >= 0 && c < n) return true;
@@ -122,297 +112,360 @@ __device__ __forceinline__ bool wrap_coord(int& c, int n, int periodic)
     return true;
 }
 
-// Loads the raw state of node i (ok = inside the box after wrapping).
-template <int ST, typename T>
-__device__ __forceinline__ void load_raw(const StepArgs& a, bool ok, uint32_t i, Raw<T>& r)
-{
-    using S = Storage<ST>;
-    using st = typename S::stype;
-    r.flag = FLAG_SOLID;
-    r.d = r.ux = r.uy = r.uz = T(0);
-    if (!ok) return;
-    // the five loads are issued together (no dependence on the flag)
-    r.flag = __ldg(a.flags + i);
-    r.d = S::load(static_cast<const st*>(a.pre[0]), i, a.inv_scale[0]);
-    r.ux = S::load(static_cast<const st*>(a.pre[1]), i, a.inv_scale[1]);
-    r.uy = S::load(static_cast<const st*>(a.pre[2]), i, a.inv_scale[2]);
-    r.uz = S::load(static_cast<const st*>(a.pre[3]), i, a.inv_scale[3]);
-}
-
-// Exchange block of in-plane direction (dx, dy), D3Q27 numbering, and the
-// D3Q19 diagonal slot of (dx, dy) (both at run time, evaluated once per thread).
-__device__ __forceinline__ int block_of(int dx, int dy)
-{
-    if (dy == 0) return dx > 0 ? 0 : 1;
-    if (dx == 0) return dy > 0 ? 2 : 3;
-    if (dx == dy) return dx > 0 ? 4 : 5;
-    return dx > 0 ? 6 : 7;
-}
-__device__ __forceinline__ int diag_of(int dx, int dy)
-{
-    if (dx == dy) return dx > 0 ? 0 : 1;
-    return dx > 0 ? 3 : 2;
-}
-
-// Where a halo-ring node stores its exports: only the in-plane directions
-// pointing into the tile. Row ring: directions (db, s) with db = 0, +1, -1;
-// column ring: (s, db). off0 is the block of db = 0; offp / offm the blocks
-// (D3Q27) or diagonal slots (D3Q19) of db = +1 / -1, as element offsets
-// within their arrays.
-struct HaloPlan {
-    int off0, offp, offm;
-    bool col;  // column ring (normal along x)
-    float sgn; // s as a multiplier (exact)
+// Raw state of the two nodes (lanes A, B) of one thread or halo slot.
+template <typename L> struct Raw2 {
+    L d, ux, uy, uz;
 };
 
-template <int Q, int NPOS>
-__device__ __forceinline__ HaloPlan halo_plan(bool col, int s, int pos)
+template <int ST, typename E>
+__device__ __forceinline__ void load_node(const StepArgs& a, bool ok, uint32_t i, E& d, E& ux, E& uy, E& uz)
 {
-    HaloPlan h;
-    h.col = col;
-    h.sgn = (float)s;
-    auto dxy = [&](int db, int& dx, int& dy) {
-        if (col) { dx = s; dy = db; } else { dx = db; dy = s; }
-    };
-    int dx, dy;
-    dxy(0, dx, dy);
-    h.off0 = block_of(dx, dy) * NPOS + pos;
-    dxy(1, dx, dy);
-    h.offp = (Q == 27 ? block_of(dx, dy) : diag_of(dx, dy)) * NPOS + pos;
-    dxy(-1, dx, dy);
-    h.offm = (Q == 27 ? block_of(dx, dy) : diag_of(dx, dy)) * NPOS + pos;
-    return h;
-}
-
-// Exports of a halo-ring node. The values are bitwise those its own tile
-// computes for the same directions (same p, same fma chain).
-template <int Q, typename T>
-__device__ __forceinline__ void store_halo_exports(V4<T>* side, T* diag, const HaloPlan& h, const Raw<T>& r,
-                                                   const StepArgs& a)
-{
-    const NodeMoments<T> m = node_moments<T>(r.d, r.ux, r.uy, r.uz, gcomp<T>(a, 0), gcomp<T>(a, 1), gcomp<T>(a, 2));
-    const T pa = T(h.sgn) * (h.col ? m.Px : m.Py);  // along the ring normal
-    const T pb = h.col ? m.Py : m.Px;               // perpendicular, in-plane
-    const bool solid = r.flag & FLAG_SOLID;
-    const T M = Marker<T>::value();
-    auto f = [&](T p) { return solid ? M : feq_scaled(m.A, m.H, p); };
-    side[h.off0] = V4<T>{f(pa - m.Pz), f(pa), f(pa + m.Pz), T(0)};
-    if constexpr (Q == 27) {
-        const T pp = pa + pb, pm = pa - pb;
-        side[h.offp] = V4<T>{f(pp - m.Pz), f(pp), f(pp + m.Pz), T(0)};
-        side[h.offm] = V4<T>{f(pm - m.Pz), f(pm), f(pm + m.Pz), T(0)};
+    if (ok) {
+        Storage<ST>::load(a.pre, i, a.inv_scale, d, ux, uy, uz);
     } else {
-        diag[h.offp] = f(pa + pb);
-        diag[h.offm] = f(pa - pb);
+        d = E(NAN);  // beyond a non-periodic face: a wall, like a solid node
+        ux = uy = uz = E(0);
     }
 }
 
-template <int Q, int ST, int TX, int TY, int MINB>
-__global__ void __launch_bounds__(TX * TY, MINB) tau1_tiled_kernel(StepArgs a, int ntx, int ntiles, int chunk)
+// Two-lane moments of a raw pair; solid lanes (drho NaN) get A = P = 0, so
+// all their outgoing values are exactly 0, and sigma = 1.
+template <typename L>
+__device__ __forceinline__ NodeMoments<L> moments_of(Raw2<L> r, const L& g0, const L& g1, const L& g2, L& sigma)
 {
-    using C = Cfg<Q, ST, TX, TY>;
-    using T = typename C::T;
-    using st = typename C::st;
-    using S = typename C::S;
+    using E = typename L::elem;
+    const bool sA = isnan(r.d.v.x), sB = isnan(r.d.v.y);
+    r.d = L(sA ? E(0) : r.d.v.x, sB ? E(0) : r.d.v.y);
+    const L keep(sA ? E(0) : E(1), sB ? E(0) : E(1));
+    sigma = L(sA ? E(1) : E(0), sB ? E(1) : E(0));
+    NodeMoments<L> m = node_moments<L>(r.d, r.ux, r.uy, r.uz, g0, g1, g2);
+    m.A = m.A * keep;
+    m.Px = m.Px * keep;
+    m.Py = m.Py * keep;
+    m.Pz = m.Pz * keep;
+    return m;
+}
+
+template <int Q, int ST, int H, int MINB>
+__global__ void __launch_bounds__(32 * H, MINB) tau1_tiled_kernel(StepArgs a, int ntx, int ntiles, int chunk)
+{
+    constexpr int TX = 32;
+    using S = Storage<ST>;
+    using E = typename S::ctype;
+    using L = typename Lanes<E>::type;
+    using C = TCfg<Q, TX, H, E>;
     using X = Xch<Q>;
-    constexpr int NPOS = C::NPOS, PW = C::PW, NB = C::NB, ND = C::ND;
+    constexpr int NPP = C::NPP, PW = C::PW, NB = C::NB, ND = C::ND;
     constexpr int NC = Weights<Q>::NCLASS;
     constexpr int KZP = kdir(0, 0, 1), KZM = kdir(0, 0, -1);
+    constexpr int TY = 2 * H;
 
     extern __shared__ __align__(32) unsigned char smem_raw[];
 
     const int tid = threadIdx.x;
-    const int tx = tid % TX, ty = tid / TX;  // a warp is one tile row: ty = warp index
-    const int my_pos = pos_of(tx, ty, PW);
-    // halo ring: warp 0 the row y = -1, warp 1 the row y = TY, warp 2 both
-    // columns (lanes 0..TY+1 at x = -1, lanes TY+2..2TY+3 at x = TX)
-    int hmode = -1, hs = 0, htx = 0, hty = 0;
-    if (ty == 0) { hmode = 0; hs = 1; htx = tx; hty = -1; }
-    else if (ty == 1) { hmode = 0; hs = -1; htx = tx; hty = TY; }
-    else if (ty == 2 && tx < TY + 2) { hmode = 1; hs = 1; htx = -1; hty = tx - 1; }
-    else if (ty == 2 && tx < 2 * (TY + 2)) { hmode = 1; hs = -1; htx = TX; hty = tx - (TY + 2) - 1; }
-    const HaloPlan hplan = halo_plan<Q, NPOS>(hmode == 1, hs, pos_of(htx, hty, PW));
+    const int tx = tid % TX, ty = tid / TX;  // pair row = warp index
+    const int my = ppos(tx, ty, PW);
 
     const int tile = blockIdx.x % ntiles;
     const int z0 = (blockIdx.x / ntiles) * chunk;
     const int z1 = min(a.nz, z0 + chunk);
     const int x0 = (tile % ntx) * TX, y0 = (tile / ntx) * TY;
-    const int gx = x0 + tx, gy = y0 + ty;
-    const bool active = gx < a.nx && gy < a.ny;
     const uint32_t nxy = (uint32_t)a.nx * (uint32_t)a.ny;
+    const int gx = x0 + tx, gyA = y0 + ty, gyB = y0 + ty + H;
+    const bool activeA = gx < a.nx && gyA < a.ny;
+    const bool activeB = gx < a.nx && gyB < a.ny;
+    const L g0(gcomp<E>(a, 0)), g1(gcomp<E>(a, 1)), g2(gcomp<E>(a, 2));
 
-    // in-plane offsets of the own and halo positions (wrapped once)
-    int wx = gx, wy = gy;
-    const bool own_xy_ok = wrap_coord(wx, a.nx, a.periodic[0]) && wrap_coord(wy, a.ny, a.periodic[1]);
-    const uint32_t own_xy = (uint32_t)wx + (uint32_t)a.nx * (uint32_t)wy;
-    int hx = x0 + htx, hy = y0 + hty;
-    const bool halo_xy_ok = hmode >= 0 && wrap_coord(hx, a.nx, a.periodic[0]) && wrap_coord(hy, a.ny, a.periodic[1]);
-    const uint32_t halo_xy = (uint32_t)hx + (uint32_t)a.nx * (uint32_t)hy;
-    const uint32_t out_xy = (uint32_t)gx + (uint32_t)a.nx * (uint32_t)gy;  // stores (active nodes only)
+    // in-plane offsets, wrapped once
+    auto xy_of = [&](int x, int y, bool& ok) -> uint32_t {
+        ok = wrap_coord(x, a.nx, a.periodic[0]) && wrap_coord(y, a.ny, a.periodic[1]);
+        return (uint32_t)x + (uint32_t)a.nx * (uint32_t)y;
+    };
+    bool okA, okB;
+    const uint32_t xyA = xy_of(gx, gyA, okA), xyB = xy_of(gx, gyB, okB);
 
-    Raw<T> r_own, r_halo;
+    // halo roles. Warp 0: halo rows below (lane A) and above (lane B).
+    // Warp 1: halo columns, lanes 0..H+1 left (x = -1), H+2..2H+3 right (x = 32).
+    const bool hrow = ty == 0;
+    const bool hcol = ty == 1 && tx < 2 * (H + 2);
+    const int hcs = tx < H + 2 ? 1 : -1;  // column ring exports directions with dx = hcs
+    const int hctx = tx < H + 2 ? -1 : TX;
+    const int hcty = tx < H + 2 ? tx - 1 : tx - (H + 2) - 1;
+    bool hokA = false, hokB = false;
+    uint32_t hxyA = 0, hxyB = 0;
+    if (hrow) {
+        hxyA = xy_of(gx, y0 - 1, hokA);
+        hxyB = xy_of(gx, y0 + TY, hokB);
+    } else if (hcol) {
+        hxyA = xy_of(x0 + hctx, y0 + hcty, hokA);
+        hxyB = xy_of(x0 + hctx, y0 + hcty + H, hokB);
+    }
+    const bool has_halo = hrow || hcol;
+    const int hc_pos = ppos(hctx, hcty, PW);
+    const int hc_b0 = hcs > 0 ? block_of(1, 0) : block_of(-1, 0);
+    const int hc_bp = (Q == 27) ? (hcs > 0 ? block_of(1, 1) : block_of(-1, 1)) : (hcs > 0 ? diag_of(1, 1) : diag_of(-1, 1));
+    const int hc_bm = (Q == 27) ? (hcs > 0 ? block_of(1, -1) : block_of(-1, -1))
+                                : (hcs > 0 ? diag_of(1, -1) : diag_of(-1, -1));
+
+    Raw2<L> r_own, r_halo;
     auto prefetch = [&](int p) {
         int gz = p;
         const bool zok = wrap_coord(gz, a.nz, a.periodic[2]);
         const uint32_t zoff = (uint32_t)gz * nxy;
-        load_raw<ST>(a, zok && own_xy_ok, zoff + own_xy, r_own);
-        if (hmode >= 0) load_raw<ST>(a, zok && halo_xy_ok, zoff + halo_xy, r_halo);
+        load_node<ST>(a, zok && okA, zoff + xyA, r_own.d.v.x, r_own.ux.v.x, r_own.uy.v.x, r_own.uz.v.x);
+        load_node<ST>(a, zok && okB, zoff + xyB, r_own.d.v.y, r_own.ux.v.y, r_own.uy.v.y, r_own.uz.v.y);
+        if (has_halo) {
+            load_node<ST>(a, zok && hokA, zoff + hxyA, r_halo.d.v.x, r_halo.ux.v.x, r_halo.uy.v.x, r_halo.uz.v.x);
+            load_node<ST>(a, zok && hokB, zoff + hxyB, r_halo.d.v.y, r_halo.ux.v.y, r_halo.uy.v.y, r_halo.uz.v.y);
+        }
     };
     prefetch(z0 - 1);
 
-    NodeAcc<T, NC> acc;          // plane p - 1, all but its c_z = -1 links
-    int flag_prev = FLAG_SOLID;  // own node flags at plane p - 1
-    T up_in[Q];   // c_z = +1 link values gathered for plane p (by k)
-    T own_in[Q];  // own outgoing (., ., +1) of plane p - 1: bounce values of its c_z = -1 links
+    NodeAcc<L, NC> acc;  // plane p - 1, all but its c_z = -1 links
+    L up_v[Q], up_s[Q];  // c_z = +1 links gathered for plane p: value, source sigma
+    L own_in[Q];         // own outgoing (., ., +1) of plane p - 1
+    bool fluidA_prev = false, fluidB_prev = false;
 #pragma unroll
-    for (int k = 0; k < Q; ++k) up_in[k] = own_in[k] = T(0);
+    for (int k = 0; k < Q; ++k) up_v[k] = up_s[k] = own_in[k] = L(E(0));
     acc.clear();
 
     for (int p = z0 - 1; p <= z1; ++p) {
         unsigned char* slot = smem_raw + (size_t)((p - z0 + 1) & 1) * C::SLOT_BYTES;
-        V4<T>* side = reinterpret_cast<V4<T>*>(slot);
-        T* diag = reinterpret_cast<T*>(slot + (size_t)NPOS * NB * sizeof(V4<T>));
+        V4<E>* L01 = reinterpret_cast<V4<E>*>(slot);
+        V2<E>* L2 = reinterpret_cast<V2<E>*>(slot + C::L01_BYTES);
+        V2<E>* DG = reinterpret_cast<V2<E>*>(slot + C::L01_BYTES + C::L2_BYTES);
+        V2<E>* SG = reinterpret_cast<V2<E>*>(slot + C::L01_BYTES + C::L2_BYTES + C::DG_BYTES);
 
-        // own outgoing values (kept in registers) and their exports
-        const Raw<T> cur = r_own;
-        T out[Q];
+        // ---- own outgoing values (registers) and exports --------------------
+        L sig;
+        L out[Q];
         {
-            const NodeMoments<T> m =
-                node_moments<T>(cur.d, cur.ux, cur.uy, cur.uz, gcomp<T>(a, 0), gcomp<T>(a, 1), gcomp<T>(a, 2));
+            const NodeMoments<L> m = moments_of(r_own, g0, g1, g2, sig);
             out[0] = m.A;
             static_for<0, (Q - 1) / 2>([&](auto ic) {
                 constexpr int K = 1 + 2 * decltype(ic)::value;  // K + 1 = inv(K)
-                const T pk = dir_dot<K, T>(m.Px, m.Py, m.Pz);
-                const T e = fma(pk * m.H, pk, m.A);
+                const L pk = dir_dot<K, L>(m.Px, m.Py, m.Pz);
+                const L e = fma(pk * m.H, pk, m.A);
                 out[K] = e + pk;
                 out[K + 1] = e - pk;
             });
-            const bool solid = cur.flag & FLAG_SOLID;
-            if (__any_sync(0xffffffffu, solid)) {
-                const T M = Marker<T>::value();
-#pragma unroll
-                for (int k = 0; k < Q; ++k) out[k] = solid ? M : out[k];
-            }
         }
+        const bool fluidA = activeA && sig.v.x == E(0), fluidB = activeB && sig.v.y == E(0);
         static_for<0, NB>([&](auto bc) {
             constexpr int b = decltype(bc)::value;
             constexpr int dx = X::dx(b), dy = X::dy(b);
-            side[b * NPOS + my_pos] = V4<T>{out[kdir(dx, dy, -1)], out[kdir(dx, dy, 0)], out[kdir(dx, dy, 1)], T(0)};
+            const L vm = out[kdir(dx, dy, -1)], v0 = out[kdir(dx, dy, 0)], vp = out[kdir(dx, dy, 1)];
+            L01[b * NPP + my] = V4<E>{vm.v.x, vm.v.y, v0.v.x, v0.v.y};
+            L2[b * NPP + my] = V2<E>{vp.v.x, vp.v.y};
         });
         static_for<0, ND>([&](auto jc) {
             constexpr int j = decltype(jc)::value;
-            diag[j * NPOS + my_pos] = out[kdir(X::ddx(j), X::ddy(j), 0)];
+            const L v = out[kdir(X::ddx(j), X::ddy(j), 0)];
+            DG[j * NPP + my] = V2<E>{v.v.x, v.v.y};
         });
-        if (hmode >= 0) store_halo_exports<Q, T>(side, diag, hplan, r_halo, a);
+        SG[my] = V2<E>{sig.v.x, sig.v.y};
+        // interior rows H-1 and H also appear in pair rows -1 (lane B) and H (lane A)
+        if (ty == H - 1) {
+            const int q = ppos(tx, -1, PW);
+            static_for<0, NB>([&](auto bc) {
+                constexpr int b = decltype(bc)::value;
+                if constexpr (X::dy(b) == 1) {
+                    L01[b * NPP + q].y = out[kdir(X::dx(b), 1, -1)].v.x;
+                    L01[b * NPP + q].w = out[kdir(X::dx(b), 1, 0)].v.x;
+                    L2[b * NPP + q].y = out[kdir(X::dx(b), 1, 1)].v.x;
+                }
+            });
+            static_for<0, ND>([&](auto jc) {
+                constexpr int j = decltype(jc)::value;
+                if constexpr (X::ddy(j) == 1) DG[j * NPP + q].y = out[kdir(X::ddx(j), 1, 0)].v.x;
+            });
+            SG[q].y = sig.v.x;
+        }
+        if (ty == 0) {
+            const int q = ppos(tx, H, PW);
+            static_for<0, NB>([&](auto bc) {
+                constexpr int b = decltype(bc)::value;
+                if constexpr (X::dy(b) == -1) {
+                    L01[b * NPP + q].x = out[kdir(X::dx(b), -1, -1)].v.y;
+                    L01[b * NPP + q].z = out[kdir(X::dx(b), -1, 0)].v.y;
+                    L2[b * NPP + q].x = out[kdir(X::dx(b), -1, 1)].v.y;
+                }
+            });
+            static_for<0, ND>([&](auto jc) {
+                constexpr int j = decltype(jc)::value;
+                if constexpr (X::ddy(j) == -1) DG[j * NPP + q].x = out[kdir(X::ddx(j), -1, 0)].v.y;
+            });
+            SG[q].x = sig.v.y;
+        }
+
+        // ---- halo exports ----------------------------------------------------
+        if (hrow) {
+            // lane A: the row below, directions with dy = +1; lane B: the row above, dy = -1
+            L hs;
+            const NodeMoments<L> m = moments_of(r_halo, g0, g1, g2, hs);
+            const L pa = m.Py * L(E(1), E(-1));
+            const L pb = m.Px;
+            auto f = [&](L pv) { return feq_scaled(m.A, m.H, pv); };
+            const int qA = ppos(tx, -1, PW), qB = ppos(tx, H, PW);
+            auto put = [&](int bA, int bB, L vm, L v0, L vp) {
+                L01[bA * NPP + qA].x = vm.v.x;
+                L01[bA * NPP + qA].z = v0.v.x;
+                L2[bA * NPP + qA].x = vp.v.x;
+                L01[bB * NPP + qB].y = vm.v.y;
+                L01[bB * NPP + qB].w = v0.v.y;
+                L2[bB * NPP + qB].y = vp.v.y;
+            };
+            put(block_of(0, 1), block_of(0, -1), f(pa - m.Pz), f(pa), f(pa + m.Pz));
+            const L pp = pa + pb, pm = pa - pb;
+            if constexpr (Q == 27) {
+                put(block_of(1, 1), block_of(1, -1), f(pp - m.Pz), f(pp), f(pp + m.Pz));
+                put(block_of(-1, 1), block_of(-1, -1), f(pm - m.Pz), f(pm), f(pm + m.Pz));
+            } else {
+                const L vpp = f(pp), vpm = f(pm);
+                DG[diag_of(1, 1) * NPP + qA].x = vpp.v.x;
+                DG[diag_of(1, -1) * NPP + qB].y = vpp.v.y;
+                DG[diag_of(-1, 1) * NPP + qA].x = vpm.v.x;
+                DG[diag_of(-1, -1) * NPP + qB].y = vpm.v.y;
+            }
+            SG[qA].x = hs.v.x;
+            SG[qB].y = hs.v.y;
+        } else if (hcol) {
+            // both lanes: directions with dx = hcs
+            L hs;
+            const NodeMoments<L> m = moments_of(r_halo, g0, g1, g2, hs);
+            const L pa = m.Px * L(E(hcs));
+            const L pb = m.Py;
+            auto f = [&](L pv) { return feq_scaled(m.A, m.H, pv); };
+            auto put = [&](int b, L vm, L v0, L vp) {
+                L01[b * NPP + hc_pos] = V4<E>{vm.v.x, vm.v.y, v0.v.x, v0.v.y};
+                L2[b * NPP + hc_pos] = V2<E>{vp.v.x, vp.v.y};
+            };
+            put(hc_b0, f(pa - m.Pz), f(pa), f(pa + m.Pz));
+            const L pp = pa + pb, pm = pa - pb;
+            if constexpr (Q == 27) {
+                put(hc_bp, f(pp - m.Pz), f(pp), f(pp + m.Pz));
+                put(hc_bm, f(pm - m.Pz), f(pm), f(pm + m.Pz));
+            } else {
+                const L vpp = f(pp), vpm = f(pm);
+                DG[hc_bp * NPP + hc_pos] = V2<E>{vpp.v.x, vpp.v.y};
+                DG[hc_bm * NPP + hc_pos] = V2<E>{vpm.v.x, vpm.v.y};
+            }
+            SG[hc_pos] = V2<E>{hs.v.x, hs.v.y};
+        }
         if (p + 1 <= z1) prefetch(p + 1);
         __syncthreads();
 
-        // gather this arrival's values by direction k
-        T dn[Q], mid[Q], up_out[Q];  // c_z = -1 (for plane p-1), 0 (plane p), +1 (plane p+1)
-        static_for<0, NB>([&](auto bc) {
-            constexpr int b = decltype(bc)::value;
-            constexpr int dx = X::dx(b), dy = X::dy(b);
-            const V4<T> v = side[b * NPOS + pos_of(tx - dx, ty - dy, PW)];
-            dn[kdir(dx, dy, -1)] = v.x;
-            mid[kdir(dx, dy, 0)] = v.y;
-            up_out[kdir(dx, dy, 1)] = v.z;
-        });
-        static_for<0, ND>([&](auto jc) {
-            constexpr int j = decltype(jc)::value;
-            constexpr int dx = X::ddx(j), dy = X::ddy(j);
-            mid[kdir(dx, dy, 0)] = diag[j * NPOS + pos_of(tx - dx, ty - dy, PW)];
-        });
-        dn[KZM] = out[KZM];
-        up_out[KZP] = out[KZP];
-
-        // plane p - 1: add its c_z = -1 links and finish it
+        // ---- gather: c_z = -1 values finish plane p - 1 ------------------------
         if (p - 1 >= z0) {
-            const bool fluid = active && !(flag_prev & FLAG_SOLID);
-            const bool wall = fluid && (flag_prev & FLAG_WALL_LINK);
-            if (__any_sync(0xffffffffu, wall)) {
-                static_for<1, Q>([&](auto kc) {
-                    constexpr int K = decltype(kc)::value;
-                    if constexpr (cvel(K, 2) == -1) {
-                        if (Marker<T>::is(dn[K])) dn[K] = own_in[inv_dir(K)];
-                    }
-                });
-            }
+            L dn_v[Q], dn_s[Q];
+            static_for<0, NB>([&](auto bc) {
+                constexpr int b = decltype(bc)::value;
+                constexpr int dx = X::dx(b), dy = X::dy(b), K = kdir(dx, dy, -1);
+                const int q = ppos(tx - dx, ty - dy, PW);
+                const V4<E> v = L01[b * NPP + q];
+                const V2<E> s = SG[q];
+                dn_v[K] = L(v.x, v.y);
+                dn_s[K] = L(s.x, s.y);
+            });
+            dn_v[KZM] = out[KZM];  // (0,0,-1): from the own node at plane p
+            dn_s[KZM] = sig;
+            // bounce values: own outgoing of plane p - 1 in direction inv(k) = (., ., +1)
             static_for<1, Q>([&](auto kc) {
                 constexpr int K = decltype(kc)::value;
-                if constexpr (cvel(K, 2) == -1) acc.template add<K>(dn[K]);
+                if constexpr (cvel(K, 2) == -1) acc.template add<K>(fma(dn_s[K], own_in[inv_dir(K)], dn_v[K]));
             });
-            if (fluid) {
-                T dd, ux, uy, uz;
-                node_finish<Q, T>(acc, dd, ux, uy, uz);
-                const uint32_t i = (uint32_t)(p - 1) * nxy + out_xy;
-                S::store(static_cast<st*>(a.post[0]), i, dd, a.scale[0]);
-                S::store(static_cast<st*>(a.post[1]), i, ux, a.scale[1]);
-                S::store(static_cast<st*>(a.post[2]), i, uy, a.scale[2]);
-                S::store(static_cast<st*>(a.post[3]), i, uz, a.scale[3]);
-            }
+            L d_, x_, y_, z_;
+            node_finish<Q, L>(acc, d_, x_, y_, z_);
+            const uint32_t zoff = (uint32_t)(p - 1) * nxy;
+            if (fluidA_prev)
+                S::store(a.post, zoff + (uint32_t)gx + (uint32_t)a.nx * (uint32_t)gyA, d_.v.x, x_.v.x, y_.v.x, z_.v.x,
+                         a.scale);
+            if (fluidB_prev)
+                S::store(a.post, zoff + (uint32_t)gx + (uint32_t)a.nx * (uint32_t)gyB, d_.v.y, x_.v.y, y_.v.y, z_.v.y,
+                         a.scale);
         }
 
-        // plane p: the c_z = +1 links gathered last arrival and this arrival's c_z = 0 links
+        // ---- plane p: the c_z = +1 links gathered last arrival, then c_z = 0 ----
         if (p >= z0 && p < z1) {
-            const bool fluid = active && !(cur.flag & FLAG_SOLID);
-            const bool wall = fluid && (cur.flag & FLAG_WALL_LINK);
-            if (__any_sync(0xffffffffu, wall)) {
-                static_for<1, Q>([&](auto kc) {
-                    constexpr int K = decltype(kc)::value;
-                    if constexpr (cvel(K, 2) == 1) {
-                        if (Marker<T>::is(up_in[K])) up_in[K] = out[inv_dir(K)];
-                    } else if constexpr (cvel(K, 2) == 0) {
-                        if (Marker<T>::is(mid[K])) mid[K] = out[inv_dir(K)];
-                    }
-                });
-            }
             acc.clear();
             acc.S[0] = out[0];
             static_for<1, Q>([&](auto kc) {
                 constexpr int K = decltype(kc)::value;
-                if constexpr (cvel(K, 2) == 1) acc.template add<K>(up_in[K]);
+                if constexpr (cvel(K, 2) == 1) acc.template add<K>(fma(up_s[K], out[inv_dir(K)], up_v[K]));
+            });
+            L mid_v[Q], mid_s[Q];
+            static_for<0, NB>([&](auto bc) {
+                constexpr int b = decltype(bc)::value;
+                constexpr int dx = X::dx(b), dy = X::dy(b), K = kdir(dx, dy, 0);
+                const int q = ppos(tx - dx, ty - dy, PW);
+                const V4<E> v = L01[b * NPP + q];
+                const V2<E> s = SG[q];
+                mid_v[K] = L(v.z, v.w);
+                mid_s[K] = L(s.x, s.y);
+            });
+            static_for<0, ND>([&](auto jc) {
+                constexpr int j = decltype(jc)::value;
+                constexpr int dx = X::ddx(j), dy = X::ddy(j), K = kdir(dx, dy, 0);
+                const int q = ppos(tx - dx, ty - dy, PW);
+                const V2<E> v = DG[j * NPP + q];
+                const V2<E> s = SG[q];
+                mid_v[K] = L(v.x, v.y);
+                mid_s[K] = L(s.x, s.y);
             });
             static_for<1, Q>([&](auto kc) {
                 constexpr int K = decltype(kc)::value;
-                if constexpr (cvel(K, 2) == 0) acc.template add<K>(mid[K]);
+                if constexpr (cvel(K, 2) == 0) acc.template add<K>(fma(mid_s[K], out[inv_dir(K)], mid_v[K]));
             });
         }
-        // carry to the next arrival
+
+        // ---- carry the c_z = +1 links of plane p + 1 -----------------------------
+        static_for<0, NB>([&](auto bc) {
+            constexpr int b = decltype(bc)::value;
+            constexpr int dx = X::dx(b), dy = X::dy(b), K = kdir(dx, dy, 1);
+            const int q = ppos(tx - dx, ty - dy, PW);
+            const V2<E> v = L2[b * NPP + q];
+            const V2<E> s = SG[q];
+            up_v[K] = L(v.x, v.y);
+            up_s[K] = L(s.x, s.y);
+        });
+        up_v[KZP] = out[KZP];
+        up_s[KZP] = sig;
         static_for<1, Q>([&](auto kc) {
             constexpr int K = decltype(kc)::value;
-            if constexpr (cvel(K, 2) == 1) {
-                up_in[K] = up_out[K];
-                own_in[K] = out[K];
-            }
+            if constexpr (cvel(K, 2) == 1) own_in[K] = out[K];
         });
-        flag_prev = cur.flag;
+        fluidA_prev = fluidA;
+        fluidB_prev = fluidB;
     }
 }
 
-template <int Q, int ST> struct TileShape;
-template <> struct TileShape<19, ST_F32> { static constexpr int TY = 8, MINB = 3; };
-template <> struct TileShape<19, ST_F16S> { static constexpr int TY = 8, MINB = 3; };
-template <> struct TileShape<19, ST_BF16S> { static constexpr int TY = 8, MINB = 3; };
-template <> struct TileShape<19, ST_F64> { static constexpr int TY = 4, MINB = 1; };
-template <> struct TileShape<27, ST_F32> { static constexpr int TY = 4, MINB = 4; };
-template <> struct TileShape<27, ST_F16S> { static constexpr int TY = 4, MINB = 4; };
-template <> struct TileShape<27, ST_BF16S> { static constexpr int TY = 4, MINB = 4; };
-template <> struct TileShape<27, ST_F64> { static constexpr int TY = 4, MINB = 1; };
+// Tile-shape variants (H = half tile height, MINB = resident blocks the
+// register budget is sized for). The autotuner picks one per handle.
+template <int Q, typename E, int V> struct Shape;
+template <> struct Shape<19, float, 0> { static constexpr int H = 4, MINB = 3; };
+template <> struct Shape<19, float, 1> { static constexpr int H = 8, MINB = 1; };
+template <> struct Shape<19, float, 2> { static constexpr int H = 4, MINB = 2; };
+template <> struct Shape<27, float, 0> { static constexpr int H = 4, MINB = 2; };
+template <> struct Shape<27, float, 1> { static constexpr int H = 8, MINB = 1; };
+template <> struct Shape<27, float, 2> { static constexpr int H = 2, MINB = 4; };
+template <int V> struct Shape<19, double, V> { static constexpr int H = 4, MINB = 1; };
+template <int V> struct Shape<27, double, V> { static constexpr int H = 2, MINB = 1; };
 
-template <int Q, int ST>
-cudaError_t launch_tiled_t(const StepArgs& a, cudaStream_t s)
+template <int Q, int ST, int V>
+cudaError_t launch_t(const StepArgs& a, cudaStream_t s)
 {
-    constexpr int TX = 32, TY = TileShape<Q, ST>::TY;
-    using C = Cfg<Q, ST, TX, TY>;
-    auto kern = tau1_tiled_kernel<Q, ST, TX, TY, TileShape<Q, ST>::MINB>;
+    using E = typename Storage<ST>::ctype;
+    constexpr int H = Shape<Q, E, V>::H;
+    using C = TCfg<Q, 32, H, E>;
+    auto kern = tau1_tiled_kernel<Q, ST, H, Shape<Q, E, V>::MINB>;
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    const int ntx = (a.nx + TX - 1) / TX;
-    const int nty = (a.ny + TY - 1) / TY;
+    const int ntx = (a.nx + 31) / 32;
+    const int nty = (a.ny + 2 * H - 1) / (2 * H);
     const int ntiles = ntx * nty;
     const int chunk = a.nz < 32 ? a.nz : 32;
     const int nchunks = (a.nz + chunk - 1) / chunk;
@@ -422,6 +475,21 @@ cudaError_t launch_tiled_t(const StepArgs& a, cudaStream_t s)
     return cudaGetLastError();
 }
 
+template <int Q, int ST>
+cudaError_t launch_v(int variant, const StepArgs& a, cudaStream_t s)
+{
+    if constexpr (ST == ST_F64) {
+        return variant == 0 ? launch_t<Q, ST, 0>(a, s) : cudaErrorInvalidValue;
+    } else {
+        switch (variant) {
+        case 0: return launch_t<Q, ST, 0>(a, s);
+        case 1: return launch_t<Q, ST, 1>(a, s);
+        case 2: return launch_t<Q, ST, 2>(a, s);
+        default: return cudaErrorInvalidValue;
+        }
+    }
+}
+
 }  // namespace
 
 bool tau1_tiled_supported(int q, int storage, int64_t n)
@@ -429,17 +497,19 @@ bool tau1_tiled_supported(int q, int storage, int64_t n)
     return (q == 19 || q == 27) && storage >= ST_F64 && storage <= ST_BF16S && n > 0 && n < ((int64_t)1 << 31);
 }
 
-cudaError_t launch_tau1_tiled(int q, int storage, const StepArgs& a, cudaStream_t s)
+int tau1_tiled_variants(int, int storage) { return storage == ST_F64 ? 1 : 3; }
+
+cudaError_t launch_tau1_tiled(int q, int storage, int variant, const StepArgs& a, cudaStream_t s)
 {
     switch (q * 10 + storage) {
-    case 190 + ST_F64: return launch_tiled_t<19, ST_F64>(a, s);
-    case 190 + ST_F32: return launch_tiled_t<19, ST_F32>(a, s);
-    case 190 + ST_F16S: return launch_tiled_t<19, ST_F16S>(a, s);
-    case 190 + ST_BF16S: return launch_tiled_t<19, ST_BF16S>(a, s);
-    case 270 + ST_F64: return launch_tiled_t<27, ST_F64>(a, s);
-    case 270 + ST_F32: return launch_tiled_t<27, ST_F32>(a, s);
-    case 270 + ST_F16S: return launch_tiled_t<27, ST_F16S>(a, s);
-    case 270 + ST_BF16S: return launch_tiled_t<27, ST_BF16S>(a, s);
+    case 190 + ST_F64: return launch_v<19, ST_F64>(variant, a, s);
+    case 190 + ST_F32: return launch_v<19, ST_F32>(variant, a, s);
+    case 190 + ST_F16S: return launch_v<19, ST_F16S>(variant, a, s);
+    case 190 + ST_BF16S: return launch_v<19, ST_BF16S>(variant, a, s);
+    case 270 + ST_F64: return launch_v<27, ST_F64>(variant, a, s);
+    case 270 + ST_F32: return launch_v<27, ST_F32>(variant, a, s);
+    case 270 + ST_F16S: return launch_v<27, ST_F16S>(variant, a, s);
+    case 270 + ST_BF16S: return launch_v<27, ST_BF16S>(variant, a, s);
     default: return cudaErrorInvalidValue;
     }
 }

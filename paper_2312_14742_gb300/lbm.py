@@ -25,9 +25,8 @@ LBM_F64, LBM_F32, LBM_F16S, LBM_BF16S = range(4)
 STORAGE = {"f64": LBM_F64, "f32": LBM_F32, "f16s": LBM_F16S, "bf16s": LBM_BF16S}
 LBM_DENSE, LBM_SPARSE = 0, 1
 LBM_SCHEME_TAU1, LBM_SCHEME_BGK = 0, 1
-LBM_KERNEL_AUTO, LBM_KERNEL_SIMPLE, LBM_KERNEL_TILED, LBM_KERNEL_TILED_SCALAR = 0, 1, 2, 3
-KERNELS = {"auto": LBM_KERNEL_AUTO, "simple": LBM_KERNEL_SIMPLE, "tiled": LBM_KERNEL_TILED,
-           "tiled_scalar": LBM_KERNEL_TILED_SCALAR}
+LBM_KERNEL_AUTO, LBM_KERNEL_SIMPLE, LBM_KERNEL_TILED = 0, 1, 2
+KERNELS = {"auto": LBM_KERNEL_AUTO, "simple": LBM_KERNEL_SIMPLE, "tiled": LBM_KERNEL_TILED}
 
 
 class lbm_tau1_config(ctypes.Structure):
