@@ -50,6 +50,7 @@ def parse():
     p.add_argument("--cpu-steps", type=int, default=3, help="oracle steps of the full box for cpu_baseline")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-bgk", action="store_true", help="skip the stored-population BGK comparator")
     return p.parse_args()
 
 
@@ -135,12 +136,16 @@ def bytes_per_fluid_node(storage: str) -> int:
     return 2 * 4 * s
 
 
+TILED_KERNEL_SOURCES = ("tau1_tiled.cu", "tau1_node.cuh", "pack2.cuh", "common.cuh", "lattice.cuh",
+                        "static_for.cuh", "kernels.h")
+
+
 def kernel_source_hash() -> str:
+    """Hash of the sources the tiled step kernel is built from."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2312_14742_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(d, f), "rb").read())
+    for f in TILED_KERNEL_SOURCES:
+        h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -287,6 +292,30 @@ def run_ours(args):
                    "what": "set_geometry(host mask) + K steps + get_fields(host, FP64) through the C ABI"}
     t.close()
 
+    # comparator: standard BGK at tau = 1 with stored populations, same box
+    bgk = None
+    if not args.no_bgk and args.storage in ("f32", "f64"):
+        from paper_2312_14742_gb300.lbm import LBM_SCHEME_BGK
+        tb = Tau1(args.q, (nx, ny, nz), storage=args.storage, periodic=(1, 1, 1), g=(args.gx, 0, 0),
+                  stream=stream, scheme=LBM_SCHEME_BGK)
+        tb.set_geometry(solid)
+        tb.step(min(args.warmup, 50))
+        kb = max(10, min(args.steps, 300))
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        tb.step(kb)
+        e1.record(stream)
+        barrier()
+        bdt = e0.elapsed_time(e1) / 1e3
+        tb.close()
+        s = 8 if args.storage == "f64" else 4
+        bbytes = 2 * args.q * s * nf  # 2 q s bytes per fluid node (Table tab_complexity)
+        bgk = {"scheme": "BGK tau=1, stored populations (pull, AB, SoA)", "value": nf * kb / bdt / 1e9,
+               "unit": "GFLUPS", "steps": kb, "ms_per_step": bdt / kb * 1e3,
+               "algorithmic_bytes_per_launch": bbytes, "achieved_GBps": bbytes / (bdt / kb) / 1e9}
+
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -313,6 +342,7 @@ def run_ours(args):
         "clocks": clocks.summary(),
         "gpu_launches": int(launches),
         "e2e": e2e,
+        "bgk_comparator": bgk,
         "stats": {"permeability": stats["permeability"], "max_abs_u": stats["max_abs_u"]},
     }
     if not args.no_cpu:

@@ -19,6 +19,9 @@ struct lbm_tau1 {
     size_t node_bytes = 0;      // bytes per node record {drho, ux, uy, uz}
     void* buf[2] = {};          // ping-pong copies of the state records
     int cur = 0;                // buf[cur] is the current (pre) state
+    void* fbuf[2] = {};         // BGK scheme: ping-pong populations [q][n]
+    int fcur = 0;
+    bool bgk = false;
     uint8_t* flags = nullptr;   // node flags
     double* red_partials = nullptr;
     double* red_out = nullptr;  // device, RED_FIELDS doubles
@@ -26,8 +29,11 @@ struct lbm_tau1 {
     bool has_geometry = false;
     int64_t step = 0;
     int64_t n_fluid = -1;
-    float scale[4] = {1, 1, 1, 1};
+    float scale[4] = {1, 1, 1, 1};      // host mirror of the 16-bit scales
     float inv_scale[4] = {1, 1, 1, 1};
+    float* dscale = nullptr;            // 16-bit storage: device {S_f, 1/S_f}
+    float* rescale_scratch = nullptr;   // 16-bit storage: maxima partials + ratios
+    float scale_host[8] = {};           // staging for scale copies
     int kernel = LBM_KERNEL_SIMPLE;
     int variant = 0;            // tile-shape variant of the tiled kernel
     int64_t launches = 0;
@@ -63,12 +69,16 @@ void free_all(lbm_tau1* h)
 {
     if (!h) return;
     cudaStreamSynchronize(h->stream);
-    for (int b = 0; b < 2; ++b)
+    for (int b = 0; b < 2; ++b) {
         if (h->buf[b]) cudaFree(h->buf[b]);
+        if (h->fbuf[b]) cudaFree(h->fbuf[b]);
+    }
     if (h->flags) cudaFree(h->flags);
     if (h->red_partials) cudaFree(h->red_partials);
     if (h->red_out) cudaFree(h->red_out);
     if (h->red_host) cudaFreeHost(h->red_host);
+    if (h->dscale) cudaFree(h->dscale);
+    if (h->rescale_scratch) cudaFree(h->rescale_scratch);
 }
 
 lbm_status check_ptr(lbm_tau1* h, const void* p, int on_device, const char* name)
@@ -94,6 +104,8 @@ void fill_args(const lbm_tau1* h, StepArgs& a)
     }
     a.pre = h->buf[h->cur];
     a.post = h->buf[h->cur ^ 1];
+    a.dscale = h->dscale;
+    a.seed = (uint32_t)(h->step + 1) * 0x9E3779B9u;
     for (int f = 0; f < 4; ++f) {
         a.inv_scale[f] = h->inv_scale[f];
         a.scale[f] = h->scale[f];
@@ -102,7 +114,85 @@ void fill_args(const lbm_tau1* h, StepArgs& a)
 
 int variant_count(const lbm_tau1* h)
 {
-    return h->kernel == LBM_KERNEL_TILED ? tau1_tiled_variants(h->cfg.q, h->cfg.storage) : 1;
+    return (!h->bgk && h->kernel == LBM_KERNEL_TILED) ? tau1_tiled_variants(h->cfg.q, h->cfg.storage) : 1;
+}
+
+constexpr int64_t RESCALE_EVERY = 64;  // 16-bit storage: steps between scale checks
+
+bool sixteen(const lbm_tau1* h) { return h->cfg.storage == LBM_F16S || h->cfg.storage == LBM_BF16S; }
+
+lbm_status upload_scales(lbm_tau1* h)
+{
+    if (!h->dscale) return LBM_OK;
+    for (int f = 0; f < 4; ++f) {
+        h->scale_host[f] = h->scale[f];
+        h->scale_host[4 + f] = h->inv_scale[f];
+    }
+    LBM_CUDA(h, cudaMemcpyAsync(h->dscale, h->scale_host, 8 * sizeof(float), cudaMemcpyDefault, h->stream),
+             "scales upload");
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream), "scales upload sync");
+    return LBM_OK;
+}
+
+// The device scales may have changed while stepping: refresh the host mirror.
+lbm_status download_scales(lbm_tau1* h)
+{
+    if (!h->dscale) return LBM_OK;
+    LBM_CUDA(h, cudaMemcpyAsync(h->scale_host, h->dscale, 8 * sizeof(float), cudaMemcpyDefault, h->stream),
+             "scales download");
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream), "scales download sync");
+    for (int f = 0; f < 4; ++f) {
+        h->scale[f] = h->scale_host[f];
+        h->inv_scale[f] = h->scale_host[4 + f];
+    }
+    return LBM_OK;
+}
+
+// Default 16-bit scales before any state is known: sized for velocities up
+// to 100 |g| (the first rescale check corrects them).
+double gmax_of(const lbm_tau1* h)
+{
+    double gmax = 0;
+    for (int d = 0; d < 3; ++d) gmax = std::fmax(gmax, std::fabs(h->cfg.g[d]));
+    return gmax;
+}
+
+// Scales of a state whose fields have maxima m (headroom rule, scale.cu).
+void set_scales(lbm_tau1* h, const double m[4])
+{
+    initial_scales(h->cfg.storage, m, gmax_of(h), h->scale);
+    for (int f = 0; f < 4; ++f) h->inv_scale[f] = 1.0f / h->scale[f];
+}
+
+// BGK: state records of the current step (before reading the state). The
+// newest copy holds post-collision populations of step n; gathering from the
+// previous copy yields the populations that arrived at step n, whose moments
+// are the state Tau1 reports. At step 0 the imported state is current.
+lbm_status bgk_refresh_state(lbm_tau1* h)
+{
+    if (!h->bgk || h->step == 0) return LBM_OK;
+    StepArgs a;
+    fill_args(h, a);
+    cudaError_t e = launch_bgk_moments(h->cfg.q, h->cfg.storage, a, h->fbuf[h->fcur ^ 1], h->buf[h->cur], h->stream);
+    ++h->launches;
+    if (e != cudaSuccess) return cuda_fail(h, e, "bgk moments kernel");
+    return LBM_OK;
+}
+
+// BGK: populations from the current state records.
+lbm_status bgk_from_state(lbm_tau1* h)
+{
+    if (!h->bgk) return LBM_OK;
+    StepArgs a;
+    fill_args(h, a);
+    // both copies: the step kernel writes fluid nodes only, so the solid
+    // nodes of the other copy must already hold their NaN marker
+    for (int b = 0; b < 2; ++b) {
+        cudaError_t e = launch_bgk_init(h->cfg.q, h->cfg.storage, a, h->buf[h->cur], h->fbuf[b], h->stream);
+        ++h->launches;
+        if (e != cudaSuccess) return cuda_fail(h, e, "bgk init kernel");
+    }
+    return LBM_OK;
 }
 
 cudaError_t launch_kernel(const lbm_tau1* h, int variant, const StepArgs& a)
@@ -115,11 +205,26 @@ lbm_status launch_step(lbm_tau1* h)
 {
     StepArgs a;
     fill_args(h, a);
+    if (h->bgk) {
+        cudaError_t e = launch_bgk_step(h->cfg.q, h->cfg.storage, a, h->fbuf[h->fcur], h->fbuf[h->fcur ^ 1], h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "bgk step launch");
+        ++h->launches;
+        h->fcur ^= 1;
+        ++h->step;
+        return LBM_OK;
+    }
     cudaError_t e = launch_kernel(h, h->variant, a);
     if (e != cudaSuccess) return cuda_fail(h, e, "tau1 step launch");
     ++h->launches;
     h->cur ^= 1;
     ++h->step;
+    if (h->dscale && h->step % RESCALE_EVERY == 0) {
+        const int64_t nb = (rescale_scratch_floats(h->n) - 4) / 4;
+        e = launch_rescale(h->cfg.storage, h->n, h->buf[h->cur], h->flags, h->dscale, h->rescale_scratch,
+                           h->rescale_scratch + 4 * nb, gmax_of(h), h->stream);
+        h->launches += 3;
+        if (e != cudaSuccess) return cuda_fail(h, e, "rescale kernels");
+    }
     return LBM_OK;
 }
 
@@ -141,7 +246,10 @@ lbm_status lbm_tau1_create(const lbm_tau1_config* cfg, lbm_tau1** out)
     if (storage_node_bytes(cfg->storage) == 0) return fail(nullptr, LBM_EINVAL, "create: bad storage");
     if (cfg->nx < 1 || cfg->ny < 1 || cfg->nz < 1) return fail(nullptr, LBM_EINVAL, "create: box sizes must be >= 1");
     if (cfg->layout != LBM_DENSE) return fail(nullptr, LBM_EINVAL, "create: only the dense layout is available");
-    if (cfg->scheme != LBM_SCHEME_TAU1) return fail(nullptr, LBM_EINVAL, "create: scheme not available");
+    if (cfg->scheme != LBM_SCHEME_TAU1 && cfg->scheme != LBM_SCHEME_BGK)
+        return fail(nullptr, LBM_EINVAL, "create: bad scheme");
+    if (cfg->scheme == LBM_SCHEME_BGK && !bgk_supported(cfg->q, cfg->storage))
+        return fail(nullptr, LBM_EINVAL, "create: the BGK scheme supports LBM_F32 and LBM_F64 storage");
     if (cfg->kernel > LBM_KERNEL_TILED) return fail(nullptr, LBM_EINVAL, "create: bad kernel");
     for (int d = 0; d < 3; ++d)
         if (!std::isfinite(cfg->g[d])) return fail(nullptr, LBM_EINVAL, "create: g must be finite");
@@ -162,11 +270,18 @@ lbm_status lbm_tau1_create(const lbm_tau1_config* cfg, lbm_tau1** out)
         return fail(nullptr, LBM_EINVAL, "create: tiled kernel not available for this lattice/storage");
     }
     cudaError_t e = cudaSuccess;
+    h->bgk = cfg->scheme == LBM_SCHEME_BGK;
     for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaMalloc(&h->buf[b], (size_t)n * h->node_bytes);
+    if (h->bgk)
+        for (int b = 0; b < 2 && e == cudaSuccess; ++b)
+            e = cudaMalloc(&h->fbuf[b], (size_t)n * cfg->q * (cfg->storage == LBM_F64 ? 8 : 4));
     if (e == cudaSuccess) e = cudaMalloc(&h->flags, (size_t)n);
     if (e == cudaSuccess) e = cudaMalloc(&h->red_partials, (size_t)reduce_blocks(n) * RED_FIELDS * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&h->red_out, RED_FIELDS * sizeof(double));
     if (e == cudaSuccess) e = cudaMallocHost(&h->red_host, RED_FIELDS * sizeof(double));
+    if (e == cudaSuccess && sixteen(h)) e = cudaMalloc(&h->dscale, 8 * sizeof(float));
+    if (e == cudaSuccess && sixteen(h))
+        e = cudaMalloc(&h->rescale_scratch, (size_t)rescale_scratch_floats(n) * sizeof(float));
     if (e != cudaSuccess) {
         lbm_status st = cuda_fail(nullptr, e, "create: device allocation");
         free_all(h);
@@ -209,7 +324,9 @@ lbm_status lbm_tau1_set_geometry(lbm_tau1* h, const uint8_t* solid, int on_devic
     ++h->launches;
     if (tmp) cudaFreeAsync(tmp, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "set_geometry: flags kernel");
-    for (int f = 0; f < 4; ++f) h->scale[f] = h->inv_scale[f] = 1.0f;
+    const double zero[4] = {0, 0, 0, 0};
+    set_scales(h, zero);
+    if (lbm_status st = upload_scales(h)) return st;
     for (int b = 0; b < 2; ++b) {
         // drho = 0, u = 0 on fluid nodes; solid nodes marked with drho = NaN
         e = launch_import_state(h->cfg.storage, h->n, nullptr, h->buf[b], h->flags, h->scale, h->stream);
@@ -217,10 +334,11 @@ lbm_status lbm_tau1_set_geometry(lbm_tau1* h, const uint8_t* solid, int on_devic
         if (e != cudaSuccess) return cuda_fail(h, e, "set_geometry: state init");
     }
     h->cur = 0;
+    h->fcur = 0;
     h->step = 0;
     h->n_fluid = -1;
     h->has_geometry = true;
-    return LBM_OK;
+    return bgk_from_state(h);
 }
 
 lbm_status lbm_tau1_set_fields(lbm_tau1* h, const double* drho, const double* ux, const double* uy,
@@ -255,23 +373,15 @@ lbm_status lbm_tau1_set_fields(lbm_tau1* h, const double* drho, const double* ux
         LBM_CUDA(h, cudaMemcpyAsync(h->red_host, h->red_out, 4 * sizeof(double), cudaMemcpyDefault, h->stream),
                  "set_fields: absmax copy");
         LBM_CUDA(h, cudaStreamSynchronize(h->stream), "set_fields: sync");
-        for (int f = 0; f < 4; ++f) {
-            const double m = h->red_host[f];
-            int ex = 0;
-            if (m > 0 && std::isfinite(m)) { std::frexp(m, &ex); ex = 12 - ex; }
-            if (h->cfg.storage == LBM_BF16S) ex = 0;
-            if (ex > 100) ex = 100;
-            if (ex < -100) ex = -100;
-            h->scale[f] = std::ldexp(1.0f, ex);
-            h->inv_scale[f] = std::ldexp(1.0f, -ex);
-        }
+        set_scales(h, h->red_host);
+        if (lbm_status st = upload_scales(h)) return st;
     }
     cudaError_t e = launch_import_state(h->cfg.storage, h->n, dsrc, h->buf[h->cur], h->flags, h->scale, h->stream);
     ++h->launches;
     if (tmp) cudaFreeAsync(tmp, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "set_fields: import kernel");
     h->step = 0;
-    return LBM_OK;
+    return bgk_from_state(h);
 }
 
 lbm_status lbm_tau1_get_fields(lbm_tau1* h, double* drho, double* ux, double* uy, double* uz, int on_device)
@@ -281,6 +391,8 @@ lbm_status lbm_tau1_get_fields(lbm_tau1* h, double* drho, double* ux, double* uy
     double* dst[4] = {drho, ux, uy, uz};
     for (int f = 0; f < 4; ++f)
         if (lbm_status st = check_ptr(h, dst[f], on_device, "get_fields field")) return st;
+    if (lbm_status st = bgk_refresh_state(h)) return st;
+    if (lbm_status st = download_scales(h)) return st;
     const size_t bytes = (size_t)h->n * sizeof(double);
     double* tmp = nullptr;
     LBM_CUDA(h, cudaMallocAsync((void**)&tmp, 4 * bytes, h->stream), "get_fields: staging allocation");
@@ -326,6 +438,11 @@ lbm_status lbm_tau1_autotune(lbm_tau1* h, int32_t trials, int32_t* chosen, float
     if (!h) return fail(nullptr, LBM_EINVAL, "autotune: NULL handle");
     if (trials < 1) return fail(h, LBM_EINVAL, "autotune: trials < 1");
     if (!h->has_geometry) return fail(h, LBM_ESTATE, "autotune: call set_geometry first");
+    if (h->bgk) {
+        if (chosen) *chosen = 0;
+        if (ms_per_step) *ms_per_step = 0.f;
+        return LBM_OK;
+    }
     // Every trial launch reads the current copy and rewrites the other one
     // without swapping, so the state is left as it was.
     StepArgs a;
@@ -366,6 +483,8 @@ lbm_status lbm_tau1_reduce(lbm_tau1* h, lbm_tau1_stats* out)
     if (!h) return fail(nullptr, LBM_EINVAL, "reduce: NULL handle");
     if (!out) return fail(h, LBM_EINVAL, "reduce: NULL output");
     if (!h->has_geometry) return fail(h, LBM_ESTATE, "reduce: call set_geometry first");
+    if (lbm_status st = bgk_refresh_state(h)) return st;
+    if (lbm_status st = download_scales(h)) return st;
     const void* f[4] = {h->buf[h->cur], nullptr, nullptr, nullptr};
     cudaError_t e = launch_reduce(h->cfg.storage, true, h->n, f, h->inv_scale, h->flags, h->cfg.g, h->red_partials,
                                   h->red_out, h->stream);

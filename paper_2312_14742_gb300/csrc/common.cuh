@@ -65,11 +65,32 @@ template <> struct Storage<ST_F32> {
     }
 };
 
+// Random bits for stochastic rounding: a counter-based hash of the node
+// index and the step seed (an odd-multiplier / xor-shift mixer), so results
+// are deterministic and the same in every kernel that stores the node.
+__device__ __forceinline__ uint32_t sr_bits(uint32_t i, uint32_t seed)
+{
+    uint32_t h = i * 0x9E3779B1u + seed;
+    h ^= h >> 15;
+    h *= 0x2C1B3C6Du;
+    h ^= h >> 12;
+    h *= 0x297A2D39u;
+    h ^= h >> 15;
+    return h;
+}
+
+// The 16-bit formats store value * S_f rounded stochastically (hardware
+// cvt.rs: the result rounds up with probability equal to the fraction of
+// the gap), so that updates smaller than half a unit in the last place still
+// move the stored state in expectation instead of stalling it; loads are
+// exact. Conversions outside the step kernels (import, re-scaling) use
+// round-to-nearest.
 template <typename H> struct Storage16 {
     using ctype = float;
     static constexpr int NODE_BYTES = 8;
     __device__ static __forceinline__ float to_f(H h);
     __device__ static __forceinline__ H from_f(float f);
+    __device__ static __forceinline__ uint32_t pack_sr(float lo, float hi, uint32_t r);
     __device__ static __forceinline__ void load(const void* base, uint32_t i, const float* inv, float& d, float& ux,
                                                 float& uy, float& uz)
     {
@@ -80,6 +101,7 @@ template <typename H> struct Storage16 {
         uy = to_f(h[2]) * inv[2];
         uz = to_f(h[3]) * inv[3];
     }
+    // round to nearest
     __device__ static __forceinline__ void store(void* base, uint32_t i, float d, float ux, float uy, float uz,
                                                  const float* sc)
     {
@@ -89,6 +111,16 @@ template <typename H> struct Storage16 {
         h[1] = from_f(ux * sc[1]);
         h[2] = from_f(uy * sc[2]);
         h[3] = from_f(uz * sc[3]);
+        static_cast<uint2*>(base)[i] = w;
+    }
+    // stochastic rounding with bits from sr_bits(i, seed)
+    __device__ static __forceinline__ void store_sr(void* base, uint32_t i, float d, float ux, float uy, float uz,
+                                                    const float* sc, uint32_t seed)
+    {
+        const uint32_t r = sr_bits(i, seed);
+        uint2 w;
+        w.x = pack_sr(d * sc[0], ux * sc[1], r);
+        w.y = pack_sr(uy * sc[2], uz * sc[3], r * 0x85EBCA6Bu + 0x165667B1u);
         static_cast<uint2*>(base)[i] = w;
     }
 };
@@ -102,8 +134,29 @@ template <> __device__ __forceinline__ __nv_bfloat16 Storage16<__nv_bfloat16>::f
 {
     return __float2bfloat16_rn(f);
 }
+// cvt.rs.*x2.f32 d, a, b: a goes to the upper half, b to the lower half.
+template <> __device__ __forceinline__ uint32_t Storage16<__half>::pack_sr(float lo, float hi, uint32_t r)
+{
+    uint32_t d;
+    asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(r));
+    return d;
+}
+template <> __device__ __forceinline__ uint32_t Storage16<__nv_bfloat16>::pack_sr(float lo, float hi, uint32_t r)
+{
+    uint32_t d;
+    asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(r));
+    return d;
+}
 template <> struct Storage<ST_F16S> : Storage16<__half> {};
 template <> struct Storage<ST_BF16S> : Storage16<__nv_bfloat16> {};
+
+// Store of a step kernel: stochastic rounding for the 16-bit formats.
+template <int ST, typename T>
+__device__ __forceinline__ void step_store(void* base, uint32_t i, T d, T ux, T uy, T uz, const float* sc, uint32_t seed)
+{
+    if constexpr (ST == ST_F16S || ST == ST_BF16S) Storage<ST>::store_sr(base, i, d, ux, uy, uz, sc, seed);
+    else Storage<ST>::store(base, i, d, ux, uy, uz, sc);
+}
 
 inline int node_bytes(int st) { return st == ST_F64 ? 32 : (st == ST_F32 ? 16 : 8); }
 
@@ -115,8 +168,23 @@ struct StepArgs {
     float gf[3];         // g rounded to FP32 (for FP32 arithmetic)
     const void* pre;     // state records read
     void* post;          // state records written (fluid nodes only)
-    float inv_scale[4];  // 16-bit storage: value = stored * inv_scale
-    float scale[4];      // 16-bit storage: stored = value * scale
+    float inv_scale[4];  // unused by the step kernels (see dscale)
+    float scale[4];
+    const float* dscale; // 16-bit storage: device float[8] = {S_f, 1/S_f}; stored = value * S_f
+    uint32_t seed;       // stochastic-rounding seed of this step
+};
+
+// Scales of the 16-bit formats, read once per thread from device memory.
+struct Scales {
+    float s[4], inv[4];
+    __device__ __forceinline__ explicit Scales(const float* d)
+    {
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            s[f] = d ? d[f] : 1.f;
+            inv[f] = d ? d[4 + f] : 1.f;
+        }
+    }
 };
 
 // Body force in the compute precision.

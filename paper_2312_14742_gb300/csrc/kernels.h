@@ -14,6 +14,21 @@ cudaError_t launch_tau1_tiled(int q, int storage, int variant, const StepArgs& a
 bool tau1_tiled_supported(int q, int storage, int64_t n);
 int tau1_tiled_variants(int q, int storage);
 
+// Standard BGK (tau = 1, stored populations) comparison kernels. Populations:
+// [q][n] in the storage type (FP32 or FP64). init: populations from state
+// records; moments: state records from the populations a step would gather.
+bool bgk_supported(int q, int storage);
+cudaError_t launch_bgk_step(int q, int storage, const StepArgs& a, const void* fin, void* fout, cudaStream_t s);
+cudaError_t launch_bgk_moments(int q, int storage, const StepArgs& a, const void* fin, void* state, cudaStream_t s);
+cudaError_t launch_bgk_init(int q, int storage, const StepArgs& a, const void* state, void* fout, cudaStream_t s);
+
+// 16-bit storage scales (device float[8]): re-chosen from the state's maxima
+// by the headroom rule and applied to the state, all on the stream.
+cudaError_t launch_rescale(int storage, int64_t n, void* state, const uint8_t* flags, float* dscale, float* partial,
+                           float* ratio, double gmax, cudaStream_t s);
+int rescale_scratch_floats(int64_t n);
+void initial_scales(int storage, const double max_abs[4], double gmax, float scale[4]);
+
 // Geometry preparation: node flags from the solid mask.
 cudaError_t launch_build_flags(int q, int nx, int ny, int nz, const int periodic[3], const uint8_t* solid,
                                uint8_t* flags, cudaStream_t s);

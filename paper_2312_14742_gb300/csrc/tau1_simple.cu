@@ -23,8 +23,9 @@ __global__ void __launch_bounds__(256) tau1_simple_kernel(StepArgs a)
     const int64_t n = (int64_t)a.nx * a.ny * a.nz;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const Scales sc(a.dscale);
     T d0, ux0, uy0, uz0;
-    S::load(a.pre, (uint32_t)i, a.inv_scale, d0, ux0, uy0, uz0);
+    S::load(a.pre, (uint32_t)i, sc.inv, d0, ux0, uy0, uz0);
     if (isnan(d0)) return;  // solid node
     const int x = (int)(i % a.nx);
     const int y = (int)((i / a.nx) % a.ny);
@@ -48,7 +49,7 @@ __global__ void __launch_bounds__(256) tau1_simple_kernel(StepArgs a)
         bool solid = true;
         if (inside) {
             const int64_t s = (int64_t)sx + (int64_t)a.nx * ((int64_t)sy + (int64_t)a.ny * sz);
-            S::load(a.pre, (uint32_t)s, a.inv_scale, d, ux, uy, uz);
+            S::load(a.pre, (uint32_t)s, sc.inv, d, ux, uy, uz);
             solid = isnan(d);
             if (solid) d = T(0);
         }
@@ -70,7 +71,7 @@ __global__ void __launch_bounds__(256) tau1_simple_kernel(StepArgs a)
 
     T d, ux, uy, uz;
     node_finish<Q, T>(acc, d, ux, uy, uz);
-    S::store(a.post, (uint32_t)i, d, ux, uy, uz, a.scale);
+    step_store<ST>(a.post, (uint32_t)i, d, ux, uy, uz, sc.s, a.seed);
 }
 
 template <int Q, int ST>

@@ -118,10 +118,11 @@ template <typename L> struct Raw2 {
 };
 
 template <int ST, typename E>
-__device__ __forceinline__ void load_node(const StepArgs& a, bool ok, uint32_t i, E& d, E& ux, E& uy, E& uz)
+__device__ __forceinline__ void load_node(const StepArgs& a, const Scales& sc, bool ok, uint32_t i, E& d, E& ux, E& uy,
+                                          E& uz)
 {
     if (ok) {
-        Storage<ST>::load(a.pre, i, a.inv_scale, d, ux, uy, uz);
+        Storage<ST>::load(a.pre, i, sc.inv, d, ux, uy, uz);
     } else {
         d = E(NAN);  // beyond a non-periodic face: a wall, like a solid node
         ux = uy = uz = E(0);
@@ -175,6 +176,7 @@ __global__ void __launch_bounds__(32 * H, MINB) tau1_tiled_kernel(StepArgs a, in
     const bool activeA = gx < a.nx && gyA < a.ny;
     const bool activeB = gx < a.nx && gyB < a.ny;
     const L g0(gcomp<E>(a, 0)), g1(gcomp<E>(a, 1)), g2(gcomp<E>(a, 2));
+    const Scales sc(a.dscale);
 
     // in-plane offsets, wrapped once
     auto xy_of = [&](int x, int y, bool& ok) -> uint32_t {
@@ -212,11 +214,11 @@ __global__ void __launch_bounds__(32 * H, MINB) tau1_tiled_kernel(StepArgs a, in
         int gz = p;
         const bool zok = wrap_coord(gz, a.nz, a.periodic[2]);
         const uint32_t zoff = (uint32_t)gz * nxy;
-        load_node<ST>(a, zok && okA, zoff + xyA, r_own.d.v.x, r_own.ux.v.x, r_own.uy.v.x, r_own.uz.v.x);
-        load_node<ST>(a, zok && okB, zoff + xyB, r_own.d.v.y, r_own.ux.v.y, r_own.uy.v.y, r_own.uz.v.y);
+        load_node<ST>(a, sc, zok && okA, zoff + xyA, r_own.d.v.x, r_own.ux.v.x, r_own.uy.v.x, r_own.uz.v.x);
+        load_node<ST>(a, sc, zok && okB, zoff + xyB, r_own.d.v.y, r_own.ux.v.y, r_own.uy.v.y, r_own.uz.v.y);
         if (has_halo) {
-            load_node<ST>(a, zok && hokA, zoff + hxyA, r_halo.d.v.x, r_halo.ux.v.x, r_halo.uy.v.x, r_halo.uz.v.x);
-            load_node<ST>(a, zok && hokB, zoff + hxyB, r_halo.d.v.y, r_halo.ux.v.y, r_halo.uy.v.y, r_halo.uz.v.y);
+            load_node<ST>(a, sc, zok && hokA, zoff + hxyA, r_halo.d.v.x, r_halo.ux.v.x, r_halo.uy.v.x, r_halo.uz.v.x);
+            load_node<ST>(a, sc, zok && hokB, zoff + hxyB, r_halo.d.v.y, r_halo.ux.v.y, r_halo.uy.v.y, r_halo.uz.v.y);
         }
     };
     prefetch(z0 - 1);
@@ -378,11 +380,11 @@ __global__ void __launch_bounds__(32 * H, MINB) tau1_tiled_kernel(StepArgs a, in
             node_finish<Q, L>(acc, d_, x_, y_, z_);
             const uint32_t zoff = (uint32_t)(p - 1) * nxy;
             if (fluidA_prev)
-                S::store(a.post, zoff + (uint32_t)gx + (uint32_t)a.nx * (uint32_t)gyA, d_.v.x, x_.v.x, y_.v.x, z_.v.x,
-                         a.scale);
+                step_store<ST>(a.post, zoff + (uint32_t)gx + (uint32_t)a.nx * (uint32_t)gyA, d_.v.x, x_.v.x, y_.v.x,
+                               z_.v.x, sc.s, a.seed);
             if (fluidB_prev)
-                S::store(a.post, zoff + (uint32_t)gx + (uint32_t)a.nx * (uint32_t)gyB, d_.v.y, x_.v.y, y_.v.y, z_.v.y,
-                         a.scale);
+                step_store<ST>(a.post, zoff + (uint32_t)gx + (uint32_t)a.nx * (uint32_t)gyB, d_.v.y, x_.v.y, y_.v.y,
+                               z_.v.y, sc.s, a.seed);
         }
 
         // ---- plane p: the c_z = +1 links gathered last arrival, then c_z = 0 ----
