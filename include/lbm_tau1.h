@@ -178,6 +178,83 @@ lbm_status lbm_tau1_set_variant(lbm_tau1* h, int32_t variant);
  * Errors: LBM_EINVAL (trials < 1), LBM_ESTATE (no geometry), LBM_ECUDA. */
 lbm_status lbm_tau1_autotune(lbm_tau1* h, int32_t trials, int32_t* chosen, float* ms_per_step);
 
+/* ---- Batches: many boxes stepped together (continuous batching) ----------
+ * No counterpart in the paper, which steps one domain at a time. A batch
+ * holds up to `capacity` live boxes of one lattice and storage format, each
+ * with its own size, periodicity, body force, geometry and state. One step of
+ * the batch advances every live box by one Tau1 step in a single persistent
+ * kernel launch; runs of `graph_steps` steps are replayed from a captured
+ * CUDA graph. Boxes are admitted while their device footprint fits in the
+ * batch's budget and released when done; admission and release edit device
+ * tables only, so captured graphs stay valid. Every box gives the same bits
+ * as it would alone in a batch (its arithmetic, step count, stochastic
+ * rounding and 16-bit scales depend on its own state only).
+ *
+ * 16-bit storage in a batch: each of the two state copies of a box has its own
+ * scales; a step decodes with the scales of the copy it reads and encodes
+ * with those of the copy it writes. For FP16 the kernel picks the next
+ * scales every 64 steps of the box from the maxima it saw while storing
+ * (headroom rule: the reference magnitude max(m_f, max m / 16, 64 |g|_max)
+ * is put at 2^12 when m_f S > 2^13 or the reference times S < 2^9). */
+typedef struct lbm_tau1_batch lbm_tau1_batch;  /* opaque, owned by the library */
+
+typedef struct lbm_tau1_batch_config {
+    int32_t q;            /* lbm_lattice of every box */
+    int32_t storage;      /* lbm_storage of every box */
+    int32_t variant;      /* tile-shape variant of the tiled kernel (as lbm_tau1_set_variant) */
+    int32_t capacity;     /* most boxes live at once, >= 1 */
+    int32_t graph_steps;  /* steps per captured graph (>= 1; 0 = 100) */
+    int32_t reserved;
+    uint64_t hbm_budget;  /* device bytes the boxes may hold; 0 = 90% of the free memory at create */
+    void* cuda_stream;    /* cudaStream_t to queue work on; NULL = legacy default stream */
+} lbm_tau1_batch_config;
+
+/* Creates an empty batch. Errors: LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA (message
+ * in lbm_tau1_last_error(NULL)). */
+lbm_status lbm_tau1_batch_create(const lbm_tau1_batch_config* cfg, lbm_tau1_batch** out);
+
+/* Device bytes one box of nx*ny*nz nodes holds in a batch of this storage:
+ * two state copies (record bytes per node: 32 F64, 16 F32, 8 F16S/BF16S) and
+ * one flag byte per node, each allocation rounded up to 256 bytes. */
+uint64_t lbm_tau1_batch_footprint(int32_t storage, int32_t nx, int32_t ny, int32_t nz);
+
+/* Admits a box: cfg gives its size, periodicity and g (cfg->q and
+ * cfg->storage must match the batch; layout dense, scheme Tau1; kernel and
+ * cuda_stream are ignored); solid is its mask as in lbm_tau1_set_geometry
+ * (host or device per on_device). The box starts from drho = 0, u = 0 at
+ * step 0 and joins the next step of the batch. Returns its slot in *slot.
+ * Errors: LBM_EBUSY (capacity reached, or its footprint exceeds the budget
+ * left; nothing changes), LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA. */
+lbm_status lbm_tau1_batch_admit(lbm_tau1_batch* b, const lbm_tau1_config* cfg, const uint8_t* solid, int on_device,
+                                int32_t* slot);
+
+/* Queues nsteps >= 0 steps of every live box and returns without waiting. */
+lbm_status lbm_tau1_batch_step(lbm_tau1_batch* b, int64_t nsteps);
+
+/* FP64 reductions (as lbm_tau1_reduce) of n live boxes slots[0..n-1] into
+ * out[0..n-1], with one synchronisation of the stream. Returns
+ * LBM_EDIVERGED, with every out[] filled, if any of them diverged. */
+lbm_status lbm_tau1_batch_stats(lbm_tau1_batch* b, int32_t n, const int32_t* slots, lbm_tau1_stats* out);
+
+/* State of a live box as doubles, as lbm_tau1_get_fields. */
+lbm_status lbm_tau1_batch_get_fields(lbm_tau1_batch* b, int32_t slot, double* drho, double* ux, double* uy,
+                                     double* uz, int on_device);
+
+/* Releases a live box: its memory returns to the budget once the queued
+ * steps that use it have run. LBM_EINVAL if slot is not live. */
+lbm_status lbm_tau1_batch_release(lbm_tau1_batch* b, int32_t slot);
+
+/* Waits for all work queued on the batch's stream. */
+lbm_status lbm_tau1_batch_synchronize(lbm_tau1_batch* b);
+
+/* Frees the batch and every box (after synchronising). NULL is a no-op. */
+lbm_status lbm_tau1_batch_destroy(lbm_tau1_batch* b);
+
+int32_t lbm_tau1_batch_live(const lbm_tau1_batch* b);           /* live boxes */
+uint64_t lbm_tau1_batch_bytes_free(const lbm_tau1_batch* b);    /* budget left */
+int64_t lbm_tau1_batch_launch_count(const lbm_tau1_batch* b);   /* kernel launches queued (graph nodes counted) */
+const char* lbm_tau1_batch_last_error(const lbm_tau1_batch* b); /* never NULL */
+
 /* ---- Reduction without allocation ------------------------------------------
  * The paper has no counterpart to this entry point; it is a service for
  * callers that cannot allocate device memory: code that works from a fixed

@@ -7,6 +7,7 @@
 #include <new>
 #include <string>
 
+#include "host.h"
 #include "kernels.h"
 #include "lbm_tau1.h"
 
@@ -229,6 +230,27 @@ lbm_status launch_step(lbm_tau1* h)
 }
 
 }  // namespace
+
+void lbm::set_create_error(const std::string& msg) { g_create_error = msg; }
+
+lbm_status lbm::fill_stats(const double* r, int64_t n_nodes, const double g[3], int64_t step, lbm_tau1_stats* out)
+{
+    std::memset(out, 0, sizeof(*out));
+    out->step = step;
+    out->n_nodes = n_nodes;
+    out->n_fluid = (int64_t)r[RED_NFLUID];
+    out->nonfinite = (int64_t)r[RED_NONFINITE];
+    out->drho_sum = r[RED_DRHO];
+    out->mass = (double)out->n_fluid + r[RED_DRHO];
+    out->mean_ux_superficial = r[RED_PX] / (double)n_nodes;
+    const double nf = out->n_fluid > 0 ? (double)out->n_fluid : 1.0;
+    out->mean_u_fluid[0] = r[RED_PX] / nf;
+    out->mean_u_fluid[1] = r[RED_PY] / nf;
+    out->mean_u_fluid[2] = r[RED_PZ] / nf;
+    out->max_abs_u = r[RED_UMAX];
+    out->permeability = g[0] != 0.0 ? (1.0 / 6.0) * out->mean_ux_superficial / g[0] : NAN;
+    return (out->nonfinite > 0 || out->max_abs_u > 0.3) ? LBM_EDIVERGED : LBM_OK;
+}
 
 extern "C" {
 
@@ -493,24 +515,9 @@ lbm_status lbm_tau1_reduce(lbm_tau1* h, lbm_tau1_stats* out)
     LBM_CUDA(h, cudaMemcpyAsync(h->red_host, h->red_out, RED_FIELDS * sizeof(double), cudaMemcpyDefault,
                                 h->stream), "reduce: copy");
     LBM_CUDA(h, cudaStreamSynchronize(h->stream), "reduce: sync");
-    const double* r = h->red_host;
-    std::memset(out, 0, sizeof(*out));
-    out->step = h->step;
-    out->n_nodes = h->n;
-    out->n_fluid = (int64_t)r[RED_NFLUID];
-    out->nonfinite = (int64_t)r[RED_NONFINITE];
-    out->drho_sum = r[RED_DRHO];
-    out->mass = (double)out->n_fluid + r[RED_DRHO];
-    out->mean_ux_superficial = r[RED_PX] / (double)h->n;
-    const double nf = out->n_fluid > 0 ? (double)out->n_fluid : 1.0;
-    out->mean_u_fluid[0] = r[RED_PX] / nf;
-    out->mean_u_fluid[1] = r[RED_PY] / nf;
-    out->mean_u_fluid[2] = r[RED_PZ] / nf;
-    out->max_abs_u = r[RED_UMAX];
-    out->permeability = h->cfg.g[0] != 0.0 ? (1.0 / 6.0) * out->mean_ux_superficial / h->cfg.g[0] : NAN;
+    const lbm_status st = fill_stats(h->red_host, h->n, h->cfg.g, h->step, out);
     h->n_fluid = out->n_fluid;
-    if (out->nonfinite > 0 || out->max_abs_u > 0.3)
-        return fail(h, LBM_EDIVERGED, "reduce: state diverged (non-finite value or |u| > 0.3)");
+    if (st == LBM_EDIVERGED) return fail(h, st, "reduce: state diverged (non-finite value or |u| > 0.3)");
     return LBM_OK;
 }
 

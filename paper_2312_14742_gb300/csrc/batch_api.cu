@@ -1,0 +1,518 @@
+// C ABI of batches: admission by device footprint, table upload, graph
+// capture and replay of the batched step, per-box reductions and state export.
+//
+// Host-side bookkeeping mirrors what the device tables hold: the live list,
+// the first work item of each live box, and each box's step count (which
+// also gives the copy holding its current state, since the copies swap every
+// step). Table edits are queued on the batch's stream from pinned staging
+// buffers, so they take effect between the steps queued before and after them.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "batch.h"
+#include "host.h"
+#include "lbm_tau1.h"
+
+using namespace lbm;
+
+namespace {
+
+constexpr int RING = 64;  // pinned staging buffers in flight
+
+struct Stage {
+    void* p = nullptr;
+    size_t cap = 0;
+    cudaEvent_t ev = nullptr;
+    bool pending = false;
+};
+
+struct Slot {
+    bool live = false;
+    lbm_tau1_config cfg{};
+    int64_t n = 0;
+    void* buf[2] = {};
+    uint8_t* flags = nullptr;
+    uint64_t bytes = 0;
+    int64_t steps = 0;
+    int items = 0;
+};
+
+uint64_t round256(uint64_t b) { return (b + 255) & ~(uint64_t)255; }
+
+}  // namespace
+
+struct lbm_tau1_batch {
+    lbm_tau1_batch_config cfg{};
+    cudaStream_t stream = nullptr;   // the caller's stream: all steps and table edits
+    cudaStream_t side = nullptr;     // admission uploads (mask copy, flags, state init)
+    cudaStream_t capture = nullptr;  // private stream for graph capture
+    cudaEvent_t side_done = nullptr;
+    std::vector<Slot> slots;
+    BatchTable* dtable = nullptr;
+    BatchDomain* ddom = nullptr;
+    int* dlive = nullptr;
+    int* dbegin = nullptr;
+    Stage ring[RING];
+    int ring_pos = 0;
+    int grid = 0, tile_h = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    uint64_t budget = 0, used = 0;
+    double* red_partials = nullptr;
+    double* red_out = nullptr;   // device [capacity][RED_FIELDS]
+    double* red_host = nullptr;  // pinned copy
+    int nlive = 0;
+    int64_t launches = 0;
+    std::string err;
+};
+
+namespace {
+
+lbm_status bfail(lbm_tau1_batch* b, lbm_status st, const std::string& msg)
+{
+    if (b) b->err = msg;
+    else set_create_error(msg);
+    return st;
+}
+
+lbm_status bcuda(lbm_tau1_batch* b, cudaError_t e, const char* what)
+{
+    std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return bfail(b, e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, m);
+}
+
+#define BCUDA(b, call, what)                                 \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return bcuda(b, e_, what);    \
+    } while (0)
+
+// A pinned staging buffer of at least `bytes`; its previous copies are complete.
+cudaError_t stage_get(lbm_tau1_batch* b, size_t bytes, Stage** out)
+{
+    Stage& s = b->ring[b->ring_pos];
+    b->ring_pos = (b->ring_pos + 1) % RING;
+    cudaError_t e = cudaSuccess;
+    if (s.pending) {
+        if ((e = cudaEventSynchronize(s.ev)) != cudaSuccess) return e;
+        s.pending = false;
+    }
+    if (s.cap < bytes) {
+        if (s.p) cudaFreeHost(s.p);
+        s.p = nullptr;
+        s.cap = 0;
+        if ((e = cudaMallocHost(&s.p, bytes)) != cudaSuccess) return e;
+        s.cap = bytes;
+    }
+    if (!s.ev && (e = cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming)) != cudaSuccess) return e;
+    *out = &s;
+    return cudaSuccess;
+}
+
+cudaError_t stage_done(Stage* s, cudaStream_t stream)
+{
+    cudaError_t e = cudaEventRecord(s->ev, stream);
+    s->pending = e == cudaSuccess;
+    return e;
+}
+
+// Rebuilds the live list and item offsets and queues their upload.
+lbm_status upload_table(lbm_tau1_batch* b)
+{
+    std::vector<int> live, begin;
+    int items = 0;
+    for (int i = 0; i < (int)b->slots.size(); ++i)
+        if (b->slots[i].live) {
+            live.push_back(i);
+            begin.push_back(items);
+            items += b->slots[i].items;
+        }
+    const int nd = (int)live.size();
+    BatchTable hdr{};
+    hdr.nitems = items;
+    hdr.ndom = nd;
+    hdr.done = 0;
+    hdr.live = b->dlive;
+    hdr.item_begin = b->dbegin;
+    hdr.dom = b->ddom;
+    const size_t lb = (size_t)nd * sizeof(int);
+    Stage* s = nullptr;
+    BCUDA(b, stage_get(b, sizeof(hdr) + 2 * lb + 16, &s), "batch: staging buffer");
+    unsigned char* p = static_cast<unsigned char*>(s->p);
+    std::memcpy(p, &hdr, sizeof(hdr));
+    if (nd) {
+        std::memcpy(p + sizeof(hdr), live.data(), lb);
+        std::memcpy(p + sizeof(hdr) + lb, begin.data(), lb);
+        BCUDA(b, cudaMemcpyAsync(b->dlive, p + sizeof(hdr), lb, cudaMemcpyHostToDevice, b->stream), "batch: table copy");
+        BCUDA(b, cudaMemcpyAsync(b->dbegin, p + sizeof(hdr) + lb, lb, cudaMemcpyHostToDevice, b->stream),
+              "batch: table copy");
+    }
+    BCUDA(b, cudaMemcpyAsync(b->dtable, p, sizeof(hdr), cudaMemcpyHostToDevice, b->stream), "batch: table copy");
+    BCUDA(b, stage_done(s, b->stream), "batch: staging event");
+    b->nlive = nd;
+    return LBM_OK;
+}
+
+lbm_status capture_graph(lbm_tau1_batch* b)
+{
+    const int k = b->cfg.graph_steps;
+    BCUDA(b, cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal), "batch: begin capture");
+    cudaError_t le = cudaSuccess;
+    for (int i = 0; i < k && le == cudaSuccess; ++i)
+        le = launch_tau1_batch(b->cfg.q, b->cfg.storage, b->cfg.variant, b->dtable, b->grid, b->capture);
+    cudaGraph_t g = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(b->capture, &g);
+    if (le != cudaSuccess || ee != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return bcuda(b, le != cudaSuccess ? le : ee, "batch: graph capture");
+    }
+    cudaGraphExec_t x = nullptr;
+    cudaError_t ie = cudaGraphInstantiate(&x, g, 0);
+    if (ie != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return bcuda(b, ie, "batch: graph instantiate");
+    }
+    b->graph = g;
+    b->gexec = x;
+    return LBM_OK;
+}
+
+void free_batch(lbm_tau1_batch* b)
+{
+    if (b->stream || b->side) {
+        cudaStreamSynchronize(b->stream);
+        if (b->side) cudaStreamSynchronize(b->side);
+    }
+    for (Slot& s : b->slots) {
+        if (s.buf[0]) cudaFree(s.buf[0]);
+        if (s.buf[1]) cudaFree(s.buf[1]);
+        if (s.flags) cudaFree(s.flags);
+    }
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (Stage& s : b->ring) {
+        if (s.ev) { cudaEventSynchronize(s.ev); cudaEventDestroy(s.ev); }
+        if (s.p) cudaFreeHost(s.p);
+    }
+    if (b->dtable) cudaFree(b->dtable);
+    if (b->ddom) cudaFree(b->ddom);
+    if (b->dlive) cudaFree(b->dlive);
+    if (b->dbegin) cudaFree(b->dbegin);
+    if (b->red_partials) cudaFree(b->red_partials);
+    if (b->red_out) cudaFree(b->red_out);
+    if (b->red_host) cudaFreeHost(b->red_host);
+    if (b->side_done) cudaEventDestroy(b->side_done);
+    if (b->side) cudaStreamDestroy(b->side);
+    if (b->capture) cudaStreamDestroy(b->capture);
+}
+
+lbm_status live_slot(lbm_tau1_batch* b, int32_t slot, const char* what)
+{
+    if (slot < 0 || slot >= (int32_t)b->slots.size() || !b->slots[slot].live)
+        return bfail(b, LBM_EINVAL, std::string(what) + ": slot is not live");
+    return LBM_OK;
+}
+
+bool sixteen_bit(int storage) { return storage == LBM_F16S || storage == LBM_BF16S; }
+
+// Device address of the inverse scales of a box's current copy (16-bit), else NULL.
+const float* dinv_of(lbm_tau1_batch* b, int32_t slot)
+{
+    if (!sixteen_bit(b->cfg.storage)) return nullptr;
+    const int c = (int)(b->slots[slot].steps & 1);
+    return &b->ddom[slot].scale[c][4];
+}
+
+}  // namespace
+
+extern "C" {
+
+uint64_t lbm_tau1_batch_footprint(int32_t storage, int32_t nx, int32_t ny, int32_t nz)
+{
+    if (storage < LBM_F64 || storage > LBM_BF16S || nx < 1 || ny < 1 || nz < 1) return 0;
+    const uint64_t n = (uint64_t)nx * (uint64_t)ny * (uint64_t)nz;
+    return 2 * round256(n * (uint64_t)node_bytes(storage)) + round256(n);
+}
+
+lbm_status lbm_tau1_batch_create(const lbm_tau1_batch_config* cfg, lbm_tau1_batch** out)
+{
+    if (out) *out = nullptr;
+    if (!cfg || !out) return bfail(nullptr, LBM_EINVAL, "batch_create: NULL argument");
+    if (cfg->q != 19 && cfg->q != 27) return bfail(nullptr, LBM_EINVAL, "batch_create: q must be 19 or 27");
+    if (cfg->storage < LBM_F64 || cfg->storage > LBM_BF16S) return bfail(nullptr, LBM_EINVAL, "batch_create: bad storage");
+    if (cfg->variant < 0 || cfg->variant >= tau1_tiled_variants(cfg->q, cfg->storage))
+        return bfail(nullptr, LBM_EINVAL, "batch_create: bad variant");
+    if (cfg->capacity < 1 || cfg->capacity > (1 << 20)) return bfail(nullptr, LBM_EINVAL, "batch_create: bad capacity");
+    if (cfg->graph_steps < 0 || cfg->graph_steps > 100000)
+        return bfail(nullptr, LBM_EINVAL, "batch_create: bad graph_steps");
+
+    lbm_tau1_batch* b = new (std::nothrow) lbm_tau1_batch();
+    if (!b) return bfail(nullptr, LBM_ENOMEM, "batch_create: host allocation failed");
+    b->cfg = *cfg;
+    if (b->cfg.graph_steps == 0) b->cfg.graph_steps = 100;
+    b->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
+    b->slots.resize((size_t)cfg->capacity);
+    const int cap = cfg->capacity;
+    cudaError_t e = batch_prepare(cfg->q, cfg->storage, cfg->variant, &b->grid, &b->tile_h);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->side_done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMalloc(&b->dtable, sizeof(BatchTable));
+    if (e == cudaSuccess) e = cudaMalloc(&b->ddom, (size_t)cap * sizeof(BatchDomain));
+    if (e == cudaSuccess) e = cudaMalloc(&b->dlive, (size_t)cap * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&b->dbegin, (size_t)cap * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&b->red_partials, (size_t)1024 * RED_FIELDS * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&b->red_out, (size_t)cap * RED_FIELDS * sizeof(double));
+    if (e == cudaSuccess) e = cudaMallocHost(&b->red_host, (size_t)cap * RED_FIELDS * sizeof(double));
+    if (e == cudaSuccess && cfg->hbm_budget == 0) {
+        size_t fr = 0, tot = 0;
+        e = cudaMemGetInfo(&fr, &tot);
+        b->budget = (uint64_t)(0.9 * (double)fr);
+    } else {
+        b->budget = cfg->hbm_budget;
+    }
+    lbm_status st = LBM_OK;
+    if (e != cudaSuccess) st = bcuda(nullptr, e, "batch_create: CUDA setup");
+    if (st == LBM_OK) {
+        st = upload_table(b);
+        if (st != LBM_OK) set_create_error(b->err);
+    }
+    if (st == LBM_OK) {
+        e = cudaStreamSynchronize(b->stream);
+        if (e != cudaSuccess) st = bcuda(nullptr, e, "batch_create: sync");
+    }
+    if (st != LBM_OK) {
+        free_batch(b);
+        delete b;
+        return st;
+    }
+    *out = b;
+    return LBM_OK;
+}
+
+lbm_status lbm_tau1_batch_admit(lbm_tau1_batch* b, const lbm_tau1_config* cfg, const uint8_t* solid, int on_device,
+                                int32_t* slot)
+{
+    if (!b) return bfail(nullptr, LBM_EINVAL, "batch_admit: NULL batch");
+    if (slot) *slot = -1;
+    if (!cfg || !solid || !slot) return bfail(b, LBM_EINVAL, "batch_admit: NULL argument");
+    if (cfg->q != b->cfg.q || cfg->storage != b->cfg.storage)
+        return bfail(b, LBM_EINVAL, "batch_admit: lattice and storage must match the batch");
+    if (cfg->layout != LBM_DENSE || cfg->scheme != LBM_SCHEME_TAU1)
+        return bfail(b, LBM_EINVAL, "batch_admit: boxes are dense-layout Tau1");
+    if (cfg->nx < 1 || cfg->ny < 1 || cfg->nz < 1) return bfail(b, LBM_EINVAL, "batch_admit: box sizes must be >= 1");
+    for (int d = 0; d < 3; ++d)
+        if (!std::isfinite(cfg->g[d])) return bfail(b, LBM_EINVAL, "batch_admit: g must be finite");
+    const int64_t n = (int64_t)cfg->nx * cfg->ny * cfg->nz;
+    if (!tau1_tiled_supported(cfg->q, cfg->storage, n)) return bfail(b, LBM_EINVAL, "batch_admit: box too large");
+    const uint64_t need = lbm_tau1_batch_footprint(cfg->storage, cfg->nx, cfg->ny, cfg->nz);
+    if (b->nlive >= b->cfg.capacity) return bfail(b, LBM_EBUSY, "batch_admit: capacity reached");
+    if (need > b->budget - b->used) return bfail(b, LBM_EBUSY, "batch_admit: footprint exceeds the budget left");
+    int id = -1;
+    for (int i = 0; i < (int)b->slots.size(); ++i)
+        if (!b->slots[i].live && !b->slots[i].buf[0]) { id = i; break; }
+    if (id < 0) return bfail(b, LBM_EBUSY, "batch_admit: no free slot");
+    Slot& s = b->slots[id];
+
+    // device memory, geometry and initial state, on the side stream
+    const size_t rb = (size_t)n * (size_t)node_bytes(cfg->storage);
+    cudaError_t e = cudaMallocAsync(&s.buf[0], rb, b->side);
+    if (e == cudaSuccess) e = cudaMallocAsync(&s.buf[1], rb, b->side);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&s.flags, (size_t)n, b->side);
+    uint8_t* tmp = nullptr;
+    const uint8_t* dsolid = solid;
+    if (e == cudaSuccess && !on_device) {
+        e = cudaMallocAsync((void**)&tmp, (size_t)n, b->side);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(tmp, solid, (size_t)n, cudaMemcpyDefault, b->side);
+        dsolid = tmp;
+    }
+    int per[3] = {cfg->periodic[0] ? 1 : 0, cfg->periodic[1] ? 1 : 0, cfg->periodic[2] ? 1 : 0};
+    if (e == cudaSuccess) e = launch_build_flags(cfg->q, cfg->nx, cfg->ny, cfg->nz, per, dsolid, s.flags, b->side);
+    if (tmp) cudaFreeAsync(tmp, b->side);
+    double gmax = 0;
+    for (int d = 0; d < 3; ++d) gmax = std::fmax(gmax, std::fabs(cfg->g[d]));
+    const double zero[4] = {0, 0, 0, 0};
+    float sc[4];
+    initial_scales(cfg->storage, zero, gmax, sc);
+    for (int c = 0; c < 2 && e == cudaSuccess; ++c)
+        e = launch_import_state(cfg->storage, n, nullptr, s.buf[c], s.flags, sc, b->side);
+    if (e == cudaSuccess) e = cudaEventRecord(b->side_done, b->side);
+    if (e != cudaSuccess) {
+        for (int c = 0; c < 2; ++c)
+            if (s.buf[c]) { cudaFreeAsync(s.buf[c], b->side); s.buf[c] = nullptr; }
+        if (s.flags) { cudaFreeAsync(s.flags, b->side); s.flags = nullptr; }
+        return bcuda(b, e, "batch_admit: upload");
+    }
+    b->launches += 3;
+
+    // the box's table record, after every queued step (the slot may have had an earlier box)
+    BatchDomain rec{};
+    rec.a.nx = cfg->nx;
+    rec.a.ny = cfg->ny;
+    rec.a.nz = cfg->nz;
+    for (int d = 0; d < 3; ++d) {
+        rec.a.periodic[d] = per[d];
+        rec.a.g[d] = cfg->g[d];
+        rec.a.gf[d] = (float)cfg->g[d];
+    }
+    rec.buf[0] = s.buf[0];
+    rec.buf[1] = s.buf[1];
+    rec.ntx = (cfg->nx + 31) / 32;
+    const int nty = (cfg->ny + b->tile_h - 1) / b->tile_h;
+    rec.ntiles = rec.ntx * nty;
+    rec.chunk = cfg->nz < 32 ? cfg->nz : 32;
+    const int nchunks = (cfg->nz + rec.chunk - 1) / rec.chunk;
+    rec.items = rec.ntiles * nchunks;
+    rec.cur = 0;
+    rec.step = 0;
+    for (int c = 0; c < 2; ++c)
+        for (int f = 0; f < 4; ++f) {
+            rec.scale[c][f] = sc[f];
+            rec.scale[c][4 + f] = 1.0f / sc[f];
+        }
+    rec.gfloor = (float)(64.0 * gmax);
+    Stage* st = nullptr;
+    BCUDA(b, stage_get(b, sizeof(rec), &st), "batch_admit: staging buffer");
+    std::memcpy(st->p, &rec, sizeof(rec));
+    BCUDA(b, cudaStreamWaitEvent(b->stream, b->side_done, 0), "batch_admit: wait");
+    BCUDA(b, cudaMemcpyAsync(b->ddom + id, st->p, sizeof(rec), cudaMemcpyHostToDevice, b->stream),
+          "batch_admit: record copy");
+    BCUDA(b, stage_done(st, b->stream), "batch_admit: staging event");
+
+    s.live = true;
+    s.cfg = *cfg;
+    s.n = n;
+    s.bytes = need;
+    s.steps = 0;
+    s.items = rec.items;
+    b->used += need;
+    if (lbm_status r = upload_table(b)) return r;
+    *slot = id;
+    return LBM_OK;
+}
+
+lbm_status lbm_tau1_batch_release(lbm_tau1_batch* b, int32_t slot)
+{
+    if (!b) return bfail(nullptr, LBM_EINVAL, "batch_release: NULL batch");
+    if (lbm_status st = live_slot(b, slot, "batch_release")) return st;
+    Slot& s = b->slots[slot];
+    s.live = false;
+    if (lbm_status st = upload_table(b)) return st;
+    // freed in stream order: after every queued step that reads them
+    for (int c = 0; c < 2; ++c) {
+        BCUDA(b, cudaFreeAsync(s.buf[c], b->stream), "batch_release: free");
+        s.buf[c] = nullptr;
+    }
+    BCUDA(b, cudaFreeAsync(s.flags, b->stream), "batch_release: free");
+    s.flags = nullptr;
+    b->used -= s.bytes;
+    s.bytes = 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_tau1_batch_step(lbm_tau1_batch* b, int64_t nsteps)
+{
+    if (!b) return bfail(nullptr, LBM_EINVAL, "batch_step: NULL batch");
+    if (nsteps < 0) return bfail(b, LBM_EINVAL, "batch_step: nsteps < 0");
+    if (b->nlive == 0 || nsteps == 0) return LBM_OK;
+    const int64_t k = b->cfg.graph_steps;
+    int64_t left = nsteps;
+    if (left >= k && !b->gexec)
+        if (lbm_status st = capture_graph(b)) return st;
+    for (; left >= k; left -= k) {
+        BCUDA(b, cudaGraphLaunch(b->gexec, b->stream), "batch_step: graph launch");
+        b->launches += k;
+    }
+    for (; left > 0; --left) {
+        BCUDA(b, launch_tau1_batch(b->cfg.q, b->cfg.storage, b->cfg.variant, b->dtable, b->grid, b->stream),
+              "batch_step: launch");
+        ++b->launches;
+    }
+    for (Slot& s : b->slots)
+        if (s.live) s.steps += nsteps;
+    return LBM_OK;
+}
+
+lbm_status lbm_tau1_batch_stats(lbm_tau1_batch* b, int32_t n, const int32_t* slots, lbm_tau1_stats* out)
+{
+    if (!b) return bfail(nullptr, LBM_EINVAL, "batch_stats: NULL batch");
+    if (n < 0 || n > b->cfg.capacity || (n > 0 && (!slots || !out)))
+        return bfail(b, LBM_EINVAL, "batch_stats: bad arguments");
+    for (int i = 0; i < n; ++i)
+        if (lbm_status st = live_slot(b, slots[i], "batch_stats")) return st;
+    for (int i = 0; i < n; ++i) {
+        const Slot& s = b->slots[slots[i]];
+        const void* f[4] = {s.buf[s.steps & 1], nullptr, nullptr, nullptr};
+        cudaError_t e = launch_reduce(b->cfg.storage, true, s.n, f, nullptr, s.flags, s.cfg.g, b->red_partials,
+                                      b->red_out + (size_t)i * RED_FIELDS, b->stream, dinv_of(b, slots[i]));
+        b->launches += 2;
+        if (e != cudaSuccess) return bcuda(b, e, "batch_stats: kernel");
+    }
+    if (n == 0) return LBM_OK;
+    BCUDA(b, cudaMemcpyAsync(b->red_host, b->red_out, (size_t)n * RED_FIELDS * sizeof(double), cudaMemcpyDefault,
+                             b->stream), "batch_stats: copy");
+    BCUDA(b, cudaStreamSynchronize(b->stream), "batch_stats: sync");
+    lbm_status worst = LBM_OK;
+    for (int i = 0; i < n; ++i) {
+        const Slot& s = b->slots[slots[i]];
+        if (fill_stats(b->red_host + (size_t)i * RED_FIELDS, s.n, s.cfg.g, s.steps, &out[i]) != LBM_OK)
+            worst = LBM_EDIVERGED;
+    }
+    if (worst != LBM_OK) return bfail(b, worst, "batch_stats: a box diverged (non-finite value or |u| > 0.3)");
+    return LBM_OK;
+}
+
+lbm_status lbm_tau1_batch_get_fields(lbm_tau1_batch* b, int32_t slot, double* drho, double* ux, double* uy,
+                                     double* uz, int on_device)
+{
+    if (!b) return bfail(nullptr, LBM_EINVAL, "batch_get_fields: NULL batch");
+    if (lbm_status st = live_slot(b, slot, "batch_get_fields")) return st;
+    const Slot& s = b->slots[slot];
+    double* dst[4] = {drho, ux, uy, uz};
+    const size_t bytes = (size_t)s.n * sizeof(double);
+    double* tmp = nullptr;
+    BCUDA(b, cudaMallocAsync((void**)&tmp, 4 * bytes, b->stream), "batch_get_fields: staging allocation");
+    double* ddst[4];
+    for (int f = 0; f < 4; ++f) ddst[f] = (on_device && dst[f]) ? dst[f] : tmp + f * s.n;
+    cudaError_t e = launch_export_state(b->cfg.storage, s.n, s.buf[s.steps & 1], ddst, s.flags, nullptr, b->stream,
+                                        dinv_of(b, slot));
+    ++b->launches;
+    if (e != cudaSuccess) { cudaFreeAsync(tmp, b->stream); return bcuda(b, e, "batch_get_fields: export kernel"); }
+    if (!on_device)
+        for (int f = 0; f < 4; ++f)
+            if (dst[f]) {
+                e = cudaMemcpyAsync(dst[f], ddst[f], bytes, cudaMemcpyDefault, b->stream);
+                if (e != cudaSuccess) { cudaFreeAsync(tmp, b->stream); return bcuda(b, e, "batch_get_fields: copy"); }
+            }
+    cudaFreeAsync(tmp, b->stream);
+    if (!on_device) BCUDA(b, cudaStreamSynchronize(b->stream), "batch_get_fields: sync");
+    return LBM_OK;
+}
+
+lbm_status lbm_tau1_batch_synchronize(lbm_tau1_batch* b)
+{
+    if (!b) return bfail(nullptr, LBM_EINVAL, "batch_synchronize: NULL batch");
+    BCUDA(b, cudaStreamSynchronize(b->stream), "batch_synchronize");
+    return LBM_OK;
+}
+
+lbm_status lbm_tau1_batch_destroy(lbm_tau1_batch* b)
+{
+    if (!b) return LBM_OK;
+    free_batch(b);
+    delete b;
+    return LBM_OK;
+}
+
+int32_t lbm_tau1_batch_live(const lbm_tau1_batch* b) { return b ? b->nlive : 0; }
+
+uint64_t lbm_tau1_batch_bytes_free(const lbm_tau1_batch* b) { return b ? b->budget - b->used : 0; }
+
+int64_t lbm_tau1_batch_launch_count(const lbm_tau1_batch* b) { return b ? b->launches : 0; }
+
+const char* lbm_tau1_batch_last_error(const lbm_tau1_batch* b) { return b ? b->err.c_str() : ""; }
+
+}  // extern "C"

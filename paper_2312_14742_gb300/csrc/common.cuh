@@ -175,14 +175,17 @@ struct StepArgs {
 };
 
 // Scales of the 16-bit formats, read once per thread from device memory.
+// inv decodes the state read, s encodes the state written; one array
+// {S, 1/S} serves both, or the read and written states have scales of their own.
 struct Scales {
     float s[4], inv[4];
-    __device__ __forceinline__ explicit Scales(const float* d)
+    __device__ __forceinline__ explicit Scales(const float* d) : Scales(d, d) {}
+    __device__ __forceinline__ Scales(const float* pre, const float* post)
     {
 #pragma unroll
         for (int f = 0; f < 4; ++f) {
-            s[f] = d ? d[f] : 1.f;
-            inv[f] = d ? d[4 + f] : 1.f;
+            s[f] = post ? post[f] : 1.f;
+            inv[f] = pre ? pre[4 + f] : 1.f;
         }
     }
 };

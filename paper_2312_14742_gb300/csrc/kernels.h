@@ -38,8 +38,10 @@ cudaError_t launch_build_flags(int q, int nx, int ny, int nz, const int periodic
 cudaError_t launch_import_state(int storage, int64_t n, const double* const src[4], void* dst,
                                 const uint8_t* flags, const float scale[4], cudaStream_t s);
 // FP64 arrays from state records; solid nodes are reported as 0.
+// inv_scale: host values (NULL = 1), replaced by the device array dinv[4] when dinv is not NULL.
 cudaError_t launch_export_state(int storage, int64_t n, const void* src, double* const dst[4],
-                                const uint8_t* flags, const float inv_scale[4], cudaStream_t s);
+                                const uint8_t* flags, const float inv_scale[4], cudaStream_t s,
+                                const float* dinv = nullptr);
 // Largest |value| per field over the fluid nodes of FP64 arrays (16-bit scales).
 cudaError_t launch_absmax_f64(int64_t n, const double* const src[4], const uint8_t* flags, double* out4,
                               double* scratch, int scratch_blocks, cudaStream_t s);
@@ -49,7 +51,9 @@ cudaError_t launch_absmax_f64(int64_t n, const double* const src[4], const uint8
 // (aos = true, fields[0] the base) or four arrays of one field each.
 enum { RED_NFLUID = 0, RED_DRHO, RED_PX, RED_PY, RED_PZ, RED_UMAX, RED_NONFINITE, RED_FIELDS = 8 };
 int reduce_blocks(int64_t n);
+// inv_scale: host values (NULL = 1), replaced by the device array dinv[4] when dinv is not NULL.
 cudaError_t launch_reduce(int storage, bool aos, int64_t n, const void* const fields[4], const float inv_scale[4],
-                          const uint8_t* flags, const double g[3], double* partials, double* out, cudaStream_t s);
+                          const uint8_t* flags, const double g[3], double* partials, double* out, cudaStream_t s,
+                          const float* dinv = nullptr);
 
 }  // namespace lbm

@@ -79,8 +79,12 @@ __global__ void import_kernel(int64_t n, F64x4 src, void* dst, const uint8_t* __
 }
 
 template <int ST>
-__global__ void export_kernel(int64_t n, const void* src, D64x4 dst, const uint8_t* __restrict__ flags, Sc4 inv)
+__global__ void export_kernel(int64_t n, const void* src, D64x4 dst, const uint8_t* __restrict__ flags, Sc4 inv,
+                              const float* dinv)
 {
+    if (dinv)
+#pragma unroll
+        for (int f = 0; f < 4; ++f) inv.v[f] = dinv[f];
     using S = Storage<ST>;
     using T = typename S::ctype;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -111,17 +115,17 @@ cudaError_t launch_import_state(int storage, int64_t n, const double* const src[
 }
 
 cudaError_t launch_export_state(int storage, int64_t n, const void* src, double* const dst[4], const uint8_t* flags,
-                                const float inv_scale[4], cudaStream_t s)
+                                const float inv_scale[4], cudaStream_t s, const float* dinv)
 {
     D64x4 b;
     Sc4 c;
-    for (int f = 0; f < 4; ++f) { b.p[f] = dst[f]; c.v[f] = inv_scale[f]; }
+    for (int f = 0; f < 4; ++f) { b.p[f] = dst[f]; c.v[f] = inv_scale ? inv_scale[f] : 1.f; }
     const unsigned g = grid_for(n, 256);
     switch (storage) {
-    case ST_F64: export_kernel<ST_F64><<<g, 256, 0, s>>>(n, src, b, flags, c); break;
-    case ST_F32: export_kernel<ST_F32><<<g, 256, 0, s>>>(n, src, b, flags, c); break;
-    case ST_F16S: export_kernel<ST_F16S><<<g, 256, 0, s>>>(n, src, b, flags, c); break;
-    case ST_BF16S: export_kernel<ST_BF16S><<<g, 256, 0, s>>>(n, src, b, flags, c); break;
+    case ST_F64: export_kernel<ST_F64><<<g, 256, 0, s>>>(n, src, b, flags, c, dinv); break;
+    case ST_F32: export_kernel<ST_F32><<<g, 256, 0, s>>>(n, src, b, flags, c, dinv); break;
+    case ST_F16S: export_kernel<ST_F16S><<<g, 256, 0, s>>>(n, src, b, flags, c, dinv); break;
+    case ST_BF16S: export_kernel<ST_BF16S><<<g, 256, 0, s>>>(n, src, b, flags, c, dinv); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

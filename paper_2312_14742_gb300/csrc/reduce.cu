@@ -80,9 +80,13 @@ template <> struct Plain<ST_BF16S> {
 };
 
 template <int ST, bool AOS>
-__global__ void __launch_bounds__(RT) reduce_pass1(int64_t n, Fields4 fl, Sc4r inv, const uint8_t* __restrict__ flags,
-                                                   double hgx, double hgy, double hgz, double* __restrict__ partials)
+__global__ void __launch_bounds__(RT) reduce_pass1(int64_t n, Fields4 fl, Sc4r inv, const float* dinv,
+                                                   const uint8_t* __restrict__ flags, double hgx, double hgy,
+                                                   double hgz, double* __restrict__ partials)
 {
+    if (dinv)
+#pragma unroll
+        for (int f = 0; f < 4; ++f) inv.v[f] = dinv[f];
     using S = Storage<ST>;
     using T = typename S::ctype;
     __shared__ double sm[RED_FIELDS][RT];
@@ -133,22 +137,23 @@ __global__ void __launch_bounds__(RT) reduce_pass2(int blocks, const double* __r
 }
 
 cudaError_t launch_reduce(int storage, bool aos, int64_t n, const void* const fields[4], const float inv_scale[4],
-                          const uint8_t* flags, const double g[3], double* partials, double* out, cudaStream_t s)
+                          const uint8_t* flags, const double g[3], double* partials, double* out, cudaStream_t s,
+                          const float* dinv)
 {
     Fields4 f;
     Sc4r sc;
-    for (int a = 0; a < 4; ++a) { f.p[a] = fields[a]; sc.v[a] = inv_scale[a]; }
+    for (int a = 0; a < 4; ++a) { f.p[a] = fields[a]; sc.v[a] = inv_scale ? inv_scale[a] : 1.f; }
     const int blocks = reduce_blocks(n);
     const double hx = 0.5 * g[0], hy = 0.5 * g[1], hz = 0.5 * g[2];
     switch (storage * 2 + (aos ? 1 : 0)) {
-    case 2 * ST_F64: reduce_pass1<ST_F64, false><<<blocks, RT, 0, s>>>(n, f, sc, flags, hx, hy, hz, partials); break;
-    case 2 * ST_F64 + 1: reduce_pass1<ST_F64, true><<<blocks, RT, 0, s>>>(n, f, sc, flags, hx, hy, hz, partials); break;
-    case 2 * ST_F32: reduce_pass1<ST_F32, false><<<blocks, RT, 0, s>>>(n, f, sc, flags, hx, hy, hz, partials); break;
-    case 2 * ST_F32 + 1: reduce_pass1<ST_F32, true><<<blocks, RT, 0, s>>>(n, f, sc, flags, hx, hy, hz, partials); break;
-    case 2 * ST_F16S: reduce_pass1<ST_F16S, false><<<blocks, RT, 0, s>>>(n, f, sc, flags, hx, hy, hz, partials); break;
-    case 2 * ST_F16S + 1: reduce_pass1<ST_F16S, true><<<blocks, RT, 0, s>>>(n, f, sc, flags, hx, hy, hz, partials); break;
-    case 2 * ST_BF16S: reduce_pass1<ST_BF16S, false><<<blocks, RT, 0, s>>>(n, f, sc, flags, hx, hy, hz, partials); break;
-    case 2 * ST_BF16S + 1: reduce_pass1<ST_BF16S, true><<<blocks, RT, 0, s>>>(n, f, sc, flags, hx, hy, hz, partials); break;
+    case 2 * ST_F64: reduce_pass1<ST_F64, false><<<blocks, RT, 0, s>>>(n, f, sc, dinv, flags, hx, hy, hz, partials); break;
+    case 2 * ST_F64 + 1: reduce_pass1<ST_F64, true><<<blocks, RT, 0, s>>>(n, f, sc, dinv, flags, hx, hy, hz, partials); break;
+    case 2 * ST_F32: reduce_pass1<ST_F32, false><<<blocks, RT, 0, s>>>(n, f, sc, dinv, flags, hx, hy, hz, partials); break;
+    case 2 * ST_F32 + 1: reduce_pass1<ST_F32, true><<<blocks, RT, 0, s>>>(n, f, sc, dinv, flags, hx, hy, hz, partials); break;
+    case 2 * ST_F16S: reduce_pass1<ST_F16S, false><<<blocks, RT, 0, s>>>(n, f, sc, dinv, flags, hx, hy, hz, partials); break;
+    case 2 * ST_F16S + 1: reduce_pass1<ST_F16S, true><<<blocks, RT, 0, s>>>(n, f, sc, dinv, flags, hx, hy, hz, partials); break;
+    case 2 * ST_BF16S: reduce_pass1<ST_BF16S, false><<<blocks, RT, 0, s>>>(n, f, sc, dinv, flags, hx, hy, hz, partials); break;
+    case 2 * ST_BF16S + 1: reduce_pass1<ST_BF16S, true><<<blocks, RT, 0, s>>>(n, f, sc, dinv, flags, hx, hy, hz, partials); break;
     default: return cudaErrorInvalidValue;
     }
     cudaError_t e = cudaGetLastError();

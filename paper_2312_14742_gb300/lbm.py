@@ -49,6 +49,12 @@ class lbm_tau1_stats(ctypes.Structure):
                 "permeability": self.permeability}
 
 
+class lbm_tau1_batch_config(ctypes.Structure):
+    _fields_ = [("q", ctypes.c_int32), ("storage", ctypes.c_int32), ("variant", ctypes.c_int32),
+                ("capacity", ctypes.c_int32), ("graph_steps", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("hbm_budget", ctypes.c_uint64), ("cuda_stream", ctypes.c_void_p)]
+
+
 _H = ctypes.c_void_p
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -70,6 +76,19 @@ SIGNATURES = {
     "lbm_tau1_variant_count": (ctypes.c_int32, [_H]),
     "lbm_tau1_set_variant": (_I, [_H, ctypes.c_int32]),
     "lbm_tau1_autotune": (_I, [_H, ctypes.c_int32, _P, _P]),
+    "lbm_tau1_batch_create": (_I, [ctypes.POINTER(lbm_tau1_batch_config), ctypes.POINTER(_H)]),
+    "lbm_tau1_batch_footprint": (ctypes.c_uint64, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
+    "lbm_tau1_batch_admit": (_I, [_H, ctypes.POINTER(lbm_tau1_config), _P, _I, ctypes.POINTER(ctypes.c_int32)]),
+    "lbm_tau1_batch_step": (_I, [_H, _I64]),
+    "lbm_tau1_batch_stats": (_I, [_H, ctypes.c_int32, _P, _P]),
+    "lbm_tau1_batch_get_fields": (_I, [_H, ctypes.c_int32, _P, _P, _P, _P, _I]),
+    "lbm_tau1_batch_release": (_I, [_H, ctypes.c_int32]),
+    "lbm_tau1_batch_synchronize": (_I, [_H]),
+    "lbm_tau1_batch_destroy": (_I, [_H]),
+    "lbm_tau1_batch_live": (ctypes.c_int32, [_H]),
+    "lbm_tau1_batch_bytes_free": (ctypes.c_uint64, [_H]),
+    "lbm_tau1_batch_launch_count": (_I64, [_H]),
+    "lbm_tau1_batch_last_error": (ctypes.c_char_p, [_H]),
     "lbm_tau1_reduce_noalloc": (_I, [ctypes.c_int32, _I64, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "lbm_tau1_noalloc_last_error": (ctypes.c_char_p, []),
 }
@@ -172,6 +191,63 @@ def lbm_tau1_reduce_noalloc(storage, n, drho, ux, uy, uz, inv_scale, solid, g, o
 
 def lbm_tau1_noalloc_last_error() -> str:
     s = _fn("lbm_tau1_noalloc_last_error")()
+    return s.decode() if s else ""
+
+
+def lbm_tau1_batch_create(cfg: lbm_tau1_batch_config) -> tuple[int, int | None]:
+    h = _H()
+    st = _fn("lbm_tau1_batch_create")(ctypes.byref(cfg), ctypes.byref(h))
+    return st, h.value
+
+
+def lbm_tau1_batch_footprint(storage: int, nx: int, ny: int, nz: int) -> int:
+    return _fn("lbm_tau1_batch_footprint")(storage, nx, ny, nz)
+
+
+def lbm_tau1_batch_admit(b, cfg: lbm_tau1_config, solid_ptr, on_device: int) -> tuple[int, int]:
+    slot = ctypes.c_int32(-1)
+    st = _fn("lbm_tau1_batch_admit")(b, ctypes.byref(cfg), solid_ptr, on_device, ctypes.byref(slot))
+    return st, slot.value
+
+
+def lbm_tau1_batch_step(b, nsteps: int) -> int:
+    return _fn("lbm_tau1_batch_step")(b, nsteps)
+
+
+def lbm_tau1_batch_stats(b, n: int, slots_ptr, stats_ptr) -> int:
+    return _fn("lbm_tau1_batch_stats")(b, n, slots_ptr, stats_ptr)
+
+
+def lbm_tau1_batch_get_fields(b, slot: int, drho, ux, uy, uz, on_device: int) -> int:
+    return _fn("lbm_tau1_batch_get_fields")(b, slot, drho, ux, uy, uz, on_device)
+
+
+def lbm_tau1_batch_release(b, slot: int) -> int:
+    return _fn("lbm_tau1_batch_release")(b, slot)
+
+
+def lbm_tau1_batch_synchronize(b) -> int:
+    return _fn("lbm_tau1_batch_synchronize")(b)
+
+
+def lbm_tau1_batch_destroy(b) -> int:
+    return _fn("lbm_tau1_batch_destroy")(b)
+
+
+def lbm_tau1_batch_live(b) -> int:
+    return _fn("lbm_tau1_batch_live")(b)
+
+
+def lbm_tau1_batch_bytes_free(b) -> int:
+    return _fn("lbm_tau1_batch_bytes_free")(b)
+
+
+def lbm_tau1_batch_launch_count(b) -> int:
+    return _fn("lbm_tau1_batch_launch_count")(b)
+
+
+def lbm_tau1_batch_last_error(b) -> str:
+    s = _fn("lbm_tau1_batch_last_error")(b)
     return s.decode() if s else ""
 
 
@@ -281,6 +357,116 @@ class Tau1:
         if getattr(self, "h", None):
             lbm_tau1_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def box_config(q: int, dims, storage: str, periodic=(1, 1, 1), g=(0.0, 0.0, 0.0)) -> lbm_tau1_config:
+    """lbm_tau1_config of one dense Tau1 box."""
+    cfg = lbm_tau1_config()
+    cfg.q, cfg.storage, cfg.layout, cfg.scheme = int(q), STORAGE[storage], LBM_DENSE, LBM_SCHEME_TAU1
+    cfg.nx, cfg.ny, cfg.nz = (int(d) for d in dims)
+    for a in range(3):
+        cfg.periodic[a] = 1 if periodic[a] else 0
+        cfg.g[a] = float(g[a])
+    return cfg
+
+
+class Batch:
+    """Boxes stepped together: ``Batch(19, "f32", capacity=64)``; ``admit`` returns a slot
+    (or None when the box does not fit now), ``step(n)`` advances every live box."""
+
+    def __init__(self, q: int, storage: str = "f32", capacity: int = 64, variant: int = 0, graph_steps: int = 100,
+                 hbm_budget: int = 0, stream=None):
+        cfg = lbm_tau1_batch_config()
+        cfg.q, cfg.storage, cfg.variant, cfg.capacity = int(q), STORAGE[storage], int(variant), int(capacity)
+        cfg.graph_steps, cfg.hbm_budget = int(graph_steps), int(hbm_budget)
+        cfg.cuda_stream = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+        st, b = lbm_tau1_batch_create(cfg)
+        if st != LBM_OK:
+            raise LbmError(st, lbm_tau1_last_error(None))
+        self.b = b
+        self.q = int(q)
+        self.storage = storage
+        self.shapes: dict[int, tuple] = {}
+
+    def _check(self, st: int) -> int:
+        if st != LBM_OK:
+            raise LbmError(st, lbm_tau1_batch_last_error(self.b))
+        return st
+
+    @staticmethod
+    def footprint(storage: str, dims) -> int:
+        return lbm_tau1_batch_footprint(STORAGE[storage], *(int(d) for d in dims))
+
+    def admit(self, solid, periodic=(1, 1, 1), g=(0.0, 0.0, 0.0)):
+        """solid: uint8 array (nz, ny, nx), host or torch CUDA. Returns the slot, or None
+        if the batch is full or the footprint does not fit (LBM_EBUSY)."""
+        dev = _is_device(solid)
+        if not dev:
+            solid = np.ascontiguousarray(solid, dtype=np.uint8)
+        nz, ny, nx = solid.shape
+        cfg = box_config(self.q, (nx, ny, nz), self.storage, periodic, g)
+        st, slot = lbm_tau1_batch_admit(self.b, cfg, _ptr(solid, dev), 1 if dev else 0)
+        if st == LBM_EBUSY:
+            return None
+        self._check(st)
+        self.shapes[slot] = (nz, ny, nx)
+        return slot
+
+    def step(self, nsteps: int = 1) -> None:
+        self._check(lbm_tau1_batch_step(self.b, int(nsteps)))
+
+    def stats(self, slots, allow_diverged: bool = False) -> list[dict]:
+        slots = list(slots)
+        n = len(slots)
+        if n == 0:
+            return []
+        arr = (ctypes.c_int32 * n)(*slots)
+        out = (lbm_tau1_stats * n)()
+        st = lbm_tau1_batch_stats(self.b, n, ctypes.cast(arr, _P), ctypes.cast(out, _P))
+        if not (st == LBM_EDIVERGED and allow_diverged):
+            self._check(st)
+        return [o.as_dict() for o in out]
+
+    def get_fields(self, slot: int):
+        arrs = [np.empty(self.shapes[slot], dtype=np.float64) for _ in range(4)]
+        self._check(lbm_tau1_batch_get_fields(self.b, int(slot), *[_ptr(a, False) for a in arrs], 0))
+        return tuple(arrs)
+
+    def release(self, slot: int) -> None:
+        self._check(lbm_tau1_batch_release(self.b, int(slot)))
+        self.shapes.pop(slot, None)
+
+    def synchronize(self) -> None:
+        self._check(lbm_tau1_batch_synchronize(self.b))
+
+    @property
+    def live(self) -> int:
+        return lbm_tau1_batch_live(self.b)
+
+    @property
+    def bytes_free(self) -> int:
+        return lbm_tau1_batch_bytes_free(self.b)
+
+    @property
+    def launch_count(self) -> int:
+        return lbm_tau1_batch_launch_count(self.b)
+
+    def close(self) -> None:
+        if getattr(self, "b", None):
+            lbm_tau1_batch_destroy(self.b)
+            self.b = None
 
     def __del__(self):
         try:

@@ -50,6 +50,57 @@ def test_struct_layouts():
     assert ctypes.sizeof(lbm.lbm_tau1_config) == 64
     assert lbm.lbm_tau1_config.g.offset == 32
     assert ctypes.sizeof(lbm.lbm_tau1_stats) == 4 * 8 + 8 * 8
+    assert ctypes.sizeof(lbm.lbm_tau1_batch_config) == 40
+
+
+STRUCTS = {
+    "lbm_tau1_config": lbm.lbm_tau1_config,
+    "lbm_tau1_stats": lbm.lbm_tau1_stats,
+    "lbm_tau1_batch_config": lbm.lbm_tau1_batch_config,
+}
+
+
+def test_struct_layouts_match_the_c_compiler(tmp_path):
+    """sizeof and every offsetof of the header's structs, printed by a C
+    program compiled against include/lbm_tau1.h, equal the binding's."""
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "lbm_tau1.h"', "int main(void) {"]
+    for name, cls in STRUCTS.items():
+        lines.append(f'printf("{name} sizeof %zu\\n", sizeof({name}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'printf("{name} {fname} %zu\\n", offsetof({name}, {fname}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    import subprocess
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {(ln.split()[0], ln.split()[1]): int(ln.split()[2]) for ln in out if ln.strip()}
+    for name, cls in STRUCTS.items():
+        assert got[(name, "sizeof")] == ctypes.sizeof(cls), name
+        for fname, _ in cls._fields_:
+            assert got[(name, fname)] == getattr(cls, fname).offset, (name, fname)
+
+
+def test_batch_footprint_and_cpu_errors(lib):
+    lbm.load()
+    # two 16-byte-record copies and one flag byte per node, each rounded up to 256 bytes
+    assert lbm.lbm_tau1_batch_footprint(lbm.LBM_F32, 32, 32, 32) == 2 * 32 ** 3 * 16 + 32 ** 3
+    assert lbm.lbm_tau1_batch_footprint(lbm.LBM_F16S, 3, 5, 7) == 2 * 1024 + 256  # 105 nodes * 8 B = 840 B
+    assert lbm.lbm_tau1_batch_footprint(lbm.LBM_F64, 10, 10, 10) == 2 * 32000 + 1024
+    assert lbm.lbm_tau1_batch_footprint(9, 4, 4, 4) == 0
+    assert lbm.lbm_tau1_batch_footprint(lbm.LBM_F32, 0, 4, 4) == 0
+    cfg = lbm.lbm_tau1_batch_config()
+    cfg.q, cfg.storage, cfg.capacity = 19, lbm.LBM_F32, 0
+    st, b = lbm.lbm_tau1_batch_create(cfg)
+    assert st == lbm.LBM_EINVAL and b is None
+    assert "capacity" in lbm.lbm_tau1_last_error(None)
+    cfg.capacity, cfg.variant = 4, 7
+    st, b = lbm.lbm_tau1_batch_create(cfg)
+    assert st == lbm.LBM_EINVAL and "variant" in lbm.lbm_tau1_last_error(None)
+    assert lbm.lbm_tau1_batch_step(None, 1) == lbm.LBM_EINVAL
+    assert lbm.lbm_tau1_batch_destroy(None) == lbm.LBM_OK
+    assert lbm.lbm_tau1_batch_live(None) == 0
 
 
 def test_abi_version_and_cpu_errors(lib):

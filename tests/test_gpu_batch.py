@@ -1,0 +1,180 @@
+"""Batches: many boxes of different sizes stepped in one persistent launch,
+K-step CUDA graphs, admission by device footprint.
+
+Every box of a batch must give exactly what the single-box path gives (FP32
+and FP64: same bits), the FP64 oracle's result within 1e-12, and the same
+bits alone as in any mix of other boxes admitted and released around it
+(all storage formats, 16-bit included: a box's scales and stochastic
+rounding depend on its own state and step count only)."""
+import numpy as np
+import pytest
+
+import lbm_inputs
+import oracle
+from paper_2312_14742_gb300 import Batch, Tau1, build
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+
+
+def boxes(seed=0):
+    """(solid, periodic, g) of boxes with ragged tiles, walls and periodic axes."""
+    out = []
+    s, _ = lbm_inputs.sphere_pack(32, 32, 32, 4.0, 0.8, lbm_inputs.workload_seed(5, seed))
+    out.append((s, (1, 1, 1), (1e-5, 0.0, 0.0)))
+    s, _ = lbm_inputs.sphere_pack(48, 40, 36, 3.0, 0.7, lbm_inputs.workload_seed(5, seed + 1))
+    s[0] = 1
+    s[-1] = 1
+    out.append((s, (1, 1, 0), (2e-5, -1e-5, 0.0)))
+    out.append((lbm_inputs.channel(20, 50, 17), (1, 1, 0), (1e-5, 0.0, 0.0)))
+    s, _ = lbm_inputs.sphere_pack(70, 9, 33, 2.5, 0.75, lbm_inputs.workload_seed(5, seed + 2))
+    out.append((s, (1, 1, 1), (0.0, 0.0, 3e-5)))
+    return out
+
+
+def single(q, storage, solid, per, g, steps):
+    nz, ny, nx = solid.shape
+    with Tau1(q, (nx, ny, nz), storage=storage, periodic=per, g=g, kernel="tiled") as t:
+        t.set_geometry(solid)
+        t.step(steps)
+        return t.get_fields(), t.reduce()
+
+
+def variants(q, storage):
+    return (0,) if storage == "f64" else (0, 1, 2)
+
+
+@pytest.mark.parametrize("q", (19, 27))
+@pytest.mark.parametrize("storage", ("f32", "f64"))
+def test_batch_equals_single_box_bitwise(q, storage):
+    """250 steps = two replays of a 100-step graph plus 50 single launches."""
+    bx = boxes()
+    refs = [single(q, storage, *b, 250) for b in bx]
+    for v in variants(q, storage):
+        with Batch(q, storage, capacity=8, variant=v, graph_steps=100) as B:
+            slots = [B.admit(s, per, g) for s, per, g in bx]
+            assert B.live == len(bx)
+            B.step(250)
+            stats = B.stats(slots)
+            for k, slot in enumerate(slots):
+                got = B.get_fields(slot)
+                for a in range(4):
+                    assert np.array_equal(got[a], refs[k][0][a]), (v, k, a)
+                assert stats[k]["step"] == 250
+                for key in ("mean_ux_superficial", "max_abs_u", "drho_sum", "n_fluid"):
+                    assert stats[k][key] == refs[k][1][key], (v, k, key)
+
+
+@pytest.mark.parametrize("q", (19, 27))
+def test_batch_fp64_matches_oracle(q):
+    solid, per, g = boxes(3)[1]
+    D = oracle.Domain(q, solid, periodic=per, g=g)
+    ref = D.tau1_run(D.zero_state(), 60)
+    with Batch(q, "f64", capacity=4, graph_steps=25) as B:
+        other = B.admit(boxes(3)[0][0], (1, 1, 1), (1e-5, 0, 0))
+        slot = B.admit(solid, per, g)
+        B.step(60)
+        got = B.get_fields(slot)
+        assert other is not None
+    umax = max(float(np.max(np.abs(ref[a]))) for a in (1, 2, 3))
+    assert float(np.max(np.abs(got[0] - ref[0]))) <= 1e-12
+    assert max(float(np.max(np.abs(got[a] - ref[a]))) for a in (1, 2, 3)) <= 1e-12 * umax
+
+
+@pytest.mark.parametrize("storage", ("f32", "f16s", "bf16s"))
+def test_same_bits_alone_and_in_a_mix(storage):
+    """Box X alone for 300 steps, and inside a batch whose other boxes come and
+    go (admitted before and after X, one released mid-run): same bits."""
+    q = 19
+    bx = boxes(7)
+    X = bx[1]
+    with Batch(q, storage, capacity=8, graph_steps=64) as A:
+        sa = A.admit(*X)
+        A.step(300)
+        alone = A.get_fields(sa)
+        alone_stats = A.stats([sa])[0]
+    with Batch(q, storage, capacity=8, graph_steps=64) as B:
+        o1 = B.admit(*bx[0])
+        o2 = B.admit(*bx[2])
+        B.step(37)
+        sx = B.admit(*X)
+        B.step(100)
+        B.release(o1)
+        o3 = B.admit(*bx[3])
+        B.step(130)
+        o4 = B.admit(*boxes(9)[0])
+        B.step(70)
+        mixed = B.get_fields(sx)
+        mixed_stats = B.stats([sx, o2, o3, o4])
+    for a in range(4):
+        assert np.array_equal(alone[a], mixed[a]), (storage, a)
+    assert mixed_stats[0]["step"] == 300 and mixed_stats[1]["step"] == 337
+    assert mixed_stats[2]["step"] == 200 and mixed_stats[3]["step"] == 70
+    assert mixed_stats[0]["mean_ux_superficial"] == alone_stats["mean_ux_superficial"]
+
+
+def test_admission_by_footprint_and_capacity():
+    bx = boxes(11)
+    fa = Batch.footprint("f32", bx[0][0].shape[::-1])
+    fb = Batch.footprint("f32", bx[1][0].shape[::-1])
+    with Batch(19, "f32", capacity=8, hbm_budget=fa + fb - 1) as B:
+        a = B.admit(*bx[0])
+        assert a is not None and B.bytes_free == fb - 1
+        assert B.admit(*bx[1]) is None  # does not fit now
+        B.step(10)
+        B.release(a)
+        assert B.bytes_free == fa + fb - 1
+        b = B.admit(*bx[1])
+        assert b is not None
+        B.step(5)
+        assert B.stats([b])[0]["step"] == 5
+    with Batch(19, "f32", capacity=2) as B:
+        assert B.admit(*bx[0]) is not None
+        assert B.admit(*bx[2]) is not None
+        assert B.admit(*bx[3]) is None  # capacity reached
+        assert B.live == 2
+
+
+def test_empty_batch_and_graph_remainders():
+    """Steps with no live box do nothing; any split of n steps into graph
+    replays and single launches gives the same bits."""
+    solid, per, g = boxes(13)[0]
+    with Batch(19, "f32", capacity=2, graph_steps=7) as B:
+        B.step(5)
+        s = B.admit(solid, per, g)
+        B.step(3)
+        B.step(7)
+        B.step(16)
+        got = B.get_fields(s)
+        assert B.stats([s])[0]["step"] == 26
+    ref, _ = single(19, "f32", solid, per, g, 26)
+    for a in range(4):
+        assert np.array_equal(got[a], ref[a])
+
+
+def test_fp16_batch_box_permeability_within_one_percent():
+    """A porous box with FP16 storage in a batch (scales chosen by the step
+    kernel's closing block): time-averaged permeability within 1% of FP64."""
+    solid, _ = lbm_inputs.sphere_pack(40, 40, 40, 4.0, 0.6, lbm_inputs.workload_seed(5, 40))
+    g = (1e-5, 0.0, 0.0)
+    with Tau1(19, (40, 40, 40), storage="f64", g=g) as t:
+        t.set_geometry(solid)
+        t.step(3000)
+        k64 = []
+        for _ in range(10):
+            t.step(50)
+            k64.append(t.reduce()["permeability"])
+        k64 = float(np.mean(k64))
+    with Batch(19, "f16s", capacity=4, graph_steps=100) as B:
+        B.admit(*boxes(17)[0])
+        s = B.admit(solid, (1, 1, 1), g)
+        B.step(3000)
+        ks = []
+        for _ in range(10):
+            B.step(50)
+            ks.append(B.stats([s])[0]["permeability"])
+    assert abs(np.mean(ks) - k64) <= 1e-2 * abs(k64), (np.mean(ks), k64)
