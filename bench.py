@@ -31,6 +31,8 @@ import numpy as np  # noqa: E402
 import lbm_inputs  # noqa: E402
 
 WORKLOAD_INDEX = 1  # seed family of the 256^3 porous workload
+SERVE_INDEX = 5     # seed family of the serving requests
+METRIC = "D3Q19 Tau1 GFLUPS & % HBM roofline; serve p50/p99 latency vs plain"
 
 
 def parse():
@@ -51,6 +53,9 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-bgk", action="store_true", help="skip the stored-population BGK comparator")
+    p.add_argument("--no-serve", action="store_true", help="skip the serving comparison")
+    p.add_argument("--serve-requests", type=int, default=60)
+    p.add_argument("--serve-max-edge", type=int, default=128)
     return p.parse_args()
 
 
@@ -136,8 +141,8 @@ def bytes_per_fluid_node(storage: str) -> int:
     return 2 * 4 * s
 
 
-TILED_KERNEL_SOURCES = ("tau1_tiled.cu", "tau1_node.cuh", "pack2.cuh", "common.cuh", "lattice.cuh",
-                        "static_for.cuh", "kernels.h")
+TILED_KERNEL_SOURCES = ("tau1_tiled.cu", "tile_column.cuh", "tau1_node.cuh", "pack2.cuh", "common.cuh",
+                        "lattice.cuh", "static_for.cuh", "kernels.h")
 
 
 def kernel_source_hash() -> str:
@@ -203,7 +208,7 @@ def run_reference(args):
     dt = time.perf_counter() - t0
     v = len(sample) * args.steps / dt / 1e9
     desc = f"{len(sample)} sampled fluid nodes per step, one FP64 oracle update each"
-    line = {"impl": "reference", "metric": f"D3Q{args.q} Tau1 GFLUPS", "value": v, "unit": "GFLUPS",
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GFLUPS",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_name(args, info)},
@@ -316,8 +321,16 @@ def run_ours(args):
                "unit": "GFLUPS", "steps": kb, "ms_per_step": bdt / kb * 1e3,
                "algorithmic_bytes_per_launch": bbytes, "achieved_GBps": bbytes / (bdt / kb) / 1e9}
 
+    # serving: Poisson permeability requests, continuously batched vs one at a time (rank 0)
+    serve_out = None
+    if rank == 0 and not args.no_serve:
+        from paper_2312_14742_gb300 import serve
+        edges = tuple(e for e in serve.EDGES if e <= args.serve_max_edge)
+        serve_out = serve.compare(args.serve_requests, lbm_inputs.workload_seed(SERVE_INDEX, 0), edges,
+                                  ("f32", "f16s"), load=0.8, calib=16)
     if rank != 0:
         if dist is not None:
+            dist.barrier()
             dist.destroy_process_group()
         return
 
@@ -327,7 +340,7 @@ def run_ours(args):
     achieved = algo_bytes / launch_s / 1e9
     value = world * nf * args.steps / dt / 1e9
     line = {
-        "metric": f"D3Q{args.q} Tau1 GFLUPS", "value": value, "unit": "GFLUPS", "n_gpus": world,
+        "metric": METRIC, "value": value, "unit": "GFLUPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.storage,
         "data": "synthetic",
@@ -344,11 +357,13 @@ def run_ours(args):
         "e2e": e2e,
         "bgk_comparator": bgk,
         "stats": {"permeability": stats["permeability"], "max_abs_u": stats["max_abs_u"]},
+        "serve": serve_out,
     }
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args, solid, args.cpu_steps)
     print(json.dumps(line), flush=True)
     if dist is not None:
+        dist.barrier()
         dist.destroy_process_group()
 
 

@@ -160,6 +160,7 @@ cudaError_t dispatch_v(int variant, bool prep, BatchTable* T, int& grid, int& ti
         case 0: return go(BatchKernel<Q, ST, 0>{});
         case 1: return go(BatchKernel<Q, ST, 1>{});
         case 2: return go(BatchKernel<Q, ST, 2>{});
+        case 3: return go(BatchKernel<Q, ST, 3>{});
         default: return cudaErrorInvalidValue;
         }
     }

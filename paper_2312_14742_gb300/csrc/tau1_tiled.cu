@@ -58,6 +58,7 @@ cudaError_t launch_v(int variant, const StepArgs& a, cudaStream_t s)
         case 0: return launch_t<Q, ST, 0>(a, s);
         case 1: return launch_t<Q, ST, 1>(a, s);
         case 2: return launch_t<Q, ST, 2>(a, s);
+        case 3: return launch_t<Q, ST, 3>(a, s);
         default: return cudaErrorInvalidValue;
         }
     }
@@ -70,7 +71,7 @@ bool tau1_tiled_supported(int q, int storage, int64_t n)
     return (q == 19 || q == 27) && storage >= ST_F64 && storage <= ST_BF16S && n > 0 && n < ((int64_t)1 << 31);
 }
 
-int tau1_tiled_variants(int, int storage) { return storage == ST_F64 ? 1 : 3; }
+int tau1_tiled_variants(int, int storage) { return storage == ST_F64 ? 1 : SHAPE_VARIANTS; }
 
 cudaError_t launch_tau1_tiled(int q, int storage, int variant, const StepArgs& a, cudaStream_t s)
 {

@@ -458,12 +458,15 @@ __device__ __forceinline__ void tile_column(const StepArgs& a, const Scales& sc,
 template <int Q, typename E, int V> struct Shape;
 template <> struct Shape<19, float, 0> { static constexpr int H = 4, MINB = 3; };
 template <> struct Shape<19, float, 1> { static constexpr int H = 8, MINB = 1; };
-template <> struct Shape<19, float, 2> { static constexpr int H = 4, MINB = 2; };
+template <> struct Shape<19, float, 2> { static constexpr int H = 8, MINB = 2; };
+template <> struct Shape<19, float, 3> { static constexpr int H = 4, MINB = 4; };
 template <> struct Shape<27, float, 0> { static constexpr int H = 4, MINB = 2; };
 template <> struct Shape<27, float, 1> { static constexpr int H = 8, MINB = 1; };
 template <> struct Shape<27, float, 2> { static constexpr int H = 2, MINB = 4; };
+template <> struct Shape<27, float, 3> { static constexpr int H = 4, MINB = 3; };
 template <int V> struct Shape<19, double, V> { static constexpr int H = 4, MINB = 1; };
 template <int V> struct Shape<27, double, V> { static constexpr int H = 2, MINB = 1; };
+constexpr int SHAPE_VARIANTS = 4;  // FP32-arithmetic formats; FP64 has one
 
 }  // namespace tile
 

@@ -45,7 +45,7 @@ def single(q, storage, solid, per, g, steps):
 
 
 def variants(q, storage):
-    return (0,) if storage == "f64" else (0, 1, 2)
+    return (0,) if storage == "f64" else (0, 1, 2, 3)
 
 
 @pytest.mark.parametrize("q", (19, 27))
