@@ -51,7 +51,7 @@ typedef enum {
     LBM_ENOMEM = 2,     /* device or host allocation failed */
     LBM_ECUDA = 3,      /* a CUDA call failed (message in last_error) */
     LBM_EDIVERGED = 4,  /* reduction saw a non-finite value or |u| > 0.3 */
-    LBM_ETIMEOUT = 5,   /* step cap reached before convergence */
+    LBM_ETIMEOUT = 5,   /* a bounded device wait (staged copy) ran out; the step results are unreliable */
     LBM_EBUSY = 6,      /* no room (batch admission) */
     LBM_ESTATE = 7      /* call out of order (e.g. step before set_geometry) */
 } lbm_status;
@@ -147,7 +147,9 @@ lbm_status lbm_tau1_step(lbm_tau1* h, int64_t nsteps);
  * node is non-finite or max|u + g/2| > 0.3. */
 lbm_status lbm_tau1_reduce(lbm_tau1* h, lbm_tau1_stats* out);
 
-/* Waits for all work queued on the handle's stream. */
+/* Waits for all work queued on the handle's stream. Returns LBM_ETIMEOUT if
+ * a staged (TMA) copy of a step kernel did not complete within its bounded
+ * wait (about one second) since the last check; reduce reports the same. */
 lbm_status lbm_tau1_synchronize(lbm_tau1* h);
 
 /* Frees the handle and its device memory (after synchronising). NULL is a no-op. */

@@ -326,6 +326,8 @@ lbm_status lbm_tau1_synchronize(lbm_tau1* h)
 {
     if (!h) return fail(nullptr, LBM_EINVAL, "synchronize: NULL handle");
     LBM_CUDA(h, cudaStreamSynchronize(h->stream), "synchronize");
+    if (unsigned t = tma_timeouts_take())
+        return fail(h, LBM_ETIMEOUT, "synchronize: " + std::to_string(t) + " staged-copy waits ran out");
     return LBM_OK;
 }
 
@@ -515,6 +517,8 @@ lbm_status lbm_tau1_reduce(lbm_tau1* h, lbm_tau1_stats* out)
     LBM_CUDA(h, cudaMemcpyAsync(h->red_host, h->red_out, RED_FIELDS * sizeof(double), cudaMemcpyDefault,
                                 h->stream), "reduce: copy");
     LBM_CUDA(h, cudaStreamSynchronize(h->stream), "reduce: sync");
+    if (unsigned t = tma_timeouts_take())
+        return fail(h, LBM_ETIMEOUT, "reduce: " + std::to_string(t) + " staged-copy waits ran out");
     const lbm_status st = fill_stats(h->red_host, h->n, h->cfg.g, h->step, out);
     h->n_fluid = out->n_fluid;
     if (st == LBM_EDIVERGED) return fail(h, st, "reduce: state diverged (non-finite value or |u| > 0.3)");

@@ -40,6 +40,14 @@ template <> struct Storage<ST_F64> {
         const double2 a = __ldg(p), b = __ldg(p + 1);
         d = a.x; ux = a.y; uy = b.x; uz = b.y;
     }
+    // one record at rec (any state space, e.g. shared memory)
+    __device__ static __forceinline__ void load_at(const void* rec, const float*, double& d, double& ux, double& uy,
+                                                   double& uz)
+    {
+        const double2* p = static_cast<const double2*>(rec);
+        const double2 a = p[0], b = p[1];
+        d = a.x; ux = a.y; uy = b.x; uz = b.y;
+    }
     __device__ static __forceinline__ void store(void* base, uint32_t i, double d, double ux, double uy, double uz,
                                                  const float*)
     {
@@ -56,6 +64,12 @@ template <> struct Storage<ST_F32> {
                                                 float& uy, float& uz)
     {
         const float4 a = __ldg(static_cast<const float4*>(base) + i);
+        d = a.x; ux = a.y; uy = a.z; uz = a.w;
+    }
+    __device__ static __forceinline__ void load_at(const void* rec, const float*, float& d, float& ux, float& uy,
+                                                   float& uz)
+    {
+        const float4 a = *static_cast<const float4*>(rec);
         d = a.x; ux = a.y; uy = a.z; uz = a.w;
     }
     __device__ static __forceinline__ void store(void* base, uint32_t i, float d, float ux, float uy, float uz,
@@ -95,6 +109,15 @@ template <typename H> struct Storage16 {
                                                 float& uy, float& uz)
     {
         const uint2 w = __ldg(static_cast<const uint2*>(base) + i);
+        decode(w, inv, d, ux, uy, uz);
+    }
+    __device__ static __forceinline__ void load_at(const void* rec, const float* inv, float& d, float& ux, float& uy,
+                                                   float& uz)
+    {
+        decode(*static_cast<const uint2*>(rec), inv, d, ux, uy, uz);
+    }
+    __device__ static __forceinline__ void decode(uint2 w, const float* inv, float& d, float& ux, float& uy, float& uz)
+    {
         const H* h = reinterpret_cast<const H*>(&w);
         d = to_f(h[0]) * inv[0];
         ux = to_f(h[1]) * inv[1];

@@ -13,6 +13,11 @@ cudaError_t launch_tau1_simple(int q, int storage, const StepArgs& a, cudaStream
 cudaError_t launch_tau1_tiled(int q, int storage, int variant, const StepArgs& a, cudaStream_t s);
 bool tau1_tiled_supported(int q, int storage, int64_t n);
 int tau1_tiled_variants(int q, int storage);
+// Staged (TMA) form of the tiled kernel: same bits; for boxes with full tiles.
+bool tau1_tiled_tma_ok(int q, int storage, int variant, const StepArgs& a);
+cudaError_t launch_tau1_tiled_tma(int q, int storage, int variant, const StepArgs& a, cudaStream_t s);
+// Waits of the staged kernel that ran out (counted on the device since the last call), then reset.
+unsigned int tma_timeouts_take();
 
 // Standard BGK (tau = 1, stored populations) comparison kernels. Populations:
 // [q][n] in the storage type (FP32 or FP64). init: populations from state

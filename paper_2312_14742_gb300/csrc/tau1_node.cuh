@@ -58,8 +58,24 @@ __device__ __forceinline__ T feq_scaled(T A, T H, T p)
     return fma(p * H, p, A) + p;
 }
 
+// Place of link K in the order in which the step kernels accumulate a node:
+// the c_z = +1 links, then c_z = 0, then c_z = -1, each group in k order.
+__host__ __device__ constexpr int acc_order(int k) { return (cvel(k, 2) == 1 ? 0 : (cvel(k, 2) == 0 ? 1 : 2)) * 32 + k; }
+
+// True when link K is the first, in that order, to add to accumulator comp
+// (0: S, 1..3: J_x..J_z) of its class. The sum then starts from that term
+// instead of from zero: one addition fewer, and only the sign of an all-zero
+// sum can differ.
+template <int Q> __host__ __device__ constexpr bool first_link(int K, int comp)
+{
+    for (int k = 1; k < Q; ++k)
+        if (dir_class(k) == dir_class(K) && (comp == 0 || cvel(k, comp - 1) != 0) && acc_order(k) < acc_order(K))
+            return false;
+    return true;
+}
+
 // Accumulators of one node: per direction class, the sum of the scaled
-// equilibria and of c times them.
+// equilibria and of c times them. add<Q, K> must be called in acc_order.
 template <typename T, int NC> struct NodeAcc {
     T S[NC];
     T Jx[NC], Jy[NC], Jz[NC];
@@ -68,14 +84,23 @@ template <typename T, int NC> struct NodeAcc {
 #pragma unroll
         for (int c = 0; c < NC; ++c) S[c] = Jx[c] = Jy[c] = Jz[c] = T(0);
     }
-    template <int K> __device__ __forceinline__ void add(T f)
+    template <int C, bool FIRST> __device__ static __forceinline__ void put(T& a, T f)
+    {
+        if constexpr (C > 0) {
+            if constexpr (FIRST) a = f;
+            else a += f;
+        } else if constexpr (C < 0) {
+            if constexpr (FIRST) a = -f;
+            else a -= f;
+        }
+    }
+    template <int Q, int K> __device__ __forceinline__ void add(T f)
     {
         constexpr int cls = dir_class(K);
-        constexpr int cx = cvel(K, 0), cy = cvel(K, 1), cz = cvel(K, 2);
-        S[cls] += f;
-        if (cx > 0) Jx[cls] += f; else if (cx < 0) Jx[cls] -= f;
-        if (cy > 0) Jy[cls] += f; else if (cy < 0) Jy[cls] -= f;
-        if (cz > 0) Jz[cls] += f; else if (cz < 0) Jz[cls] -= f;
+        put<1, first_link<Q>(K, 0)>(S[cls], f);
+        put<cvel(K, 0), first_link<Q>(K, 1)>(Jx[cls], f);
+        put<cvel(K, 1), first_link<Q>(K, 2)>(Jy[cls], f);
+        put<cvel(K, 2), first_link<Q>(K, 3)>(Jz[cls], f);
     }
 };
 

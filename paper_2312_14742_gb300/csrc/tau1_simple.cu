@@ -34,7 +34,6 @@ __global__ void __launch_bounds__(256) tau1_simple_kernel(StepArgs a)
 
     const NodeMoments<T> own = node_moments<T>(d0, ux0, uy0, uz0, gx, gy, gz);
     NodeAcc<T, Weights<Q>::NCLASS> acc;
-    acc.clear();
     acc.S[0] = own.A;  // rest direction: p = 0
 
     // one link: the equilibrium arriving along c_K, or the reflected one
@@ -63,7 +62,7 @@ __global__ void __launch_bounds__(256) tau1_simple_kernel(StepArgs a)
         const T v = feq_scaled(m.A, m.H, dir_dot<K, T>(m.Px, m.Py, m.Pz));
         // reflected population: own state in direction inv(k), p(inv k) = -p(k)
         const T b = feq_scaled(own.A, own.H, -dir_dot<K, T>(own.Px, own.Py, own.Pz));
-        acc.template add<K>(fma(solid ? T(1) : T(0), b, v));
+        acc.template add<Q, K>(fma(solid ? T(1) : T(0), b, v));
     };
     static_for<1, Q>([&](auto kc) { if constexpr (cvel(decltype(kc)::value, 2) == 1) link(kc); });
     static_for<1, Q>([&](auto kc) { if constexpr (cvel(decltype(kc)::value, 2) == 0) link(kc); });

@@ -75,6 +75,7 @@ int tau1_tiled_variants(int, int storage) { return storage == ST_F64 ? 1 : SHAPE
 
 cudaError_t launch_tau1_tiled(int q, int storage, int variant, const StepArgs& a, cudaStream_t s)
 {
+    if (tau1_tiled_tma_ok(q, storage, variant, a)) return launch_tau1_tiled_tma(q, storage, variant, a, s);
     switch (q * 10 + storage) {
     case 190 + ST_F64: return launch_v<19, ST_F64>(variant, a, s);
     case 190 + ST_F32: return launch_v<19, ST_F32>(variant, a, s);

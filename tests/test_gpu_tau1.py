@@ -238,8 +238,11 @@ def test_divergence_is_reported_not_trapped():
 
 @pytest.mark.parametrize("storage", ("f32", "f64", "f16s", "bf16s"))
 @pytest.mark.parametrize("q", (19, 27))
-@pytest.mark.parametrize("dims,per", [((64, 40, 33), (1, 1, 1)), ((45, 19, 21), (1, 0, 1)), ((7, 70, 9), (0, 1, 0))])
+@pytest.mark.parametrize("dims,per", [((64, 40, 33), (1, 1, 1)), ((45, 19, 21), (1, 0, 1)), ((7, 70, 9), (0, 1, 0)),
+                                      ((64, 48, 40), (1, 0, 1)), ((96, 32, 20), (0, 1, 1))])
 def test_tiled_bitwise_equals_simple(q, dims, per, storage):
+    """Boxes with full tiles (nx a multiple of 32, ny of the tile height) run the
+    staged (TMA) form of the tiled kernel, the others the register form."""
     nx, ny, nz = dims
     solid, _ = lbm_inputs.sphere_pack(nx, ny, nz, 3.0, 0.8, 4242 + nx)
     st = lbm_inputs.random_fields(solid.shape, 17, 2e-3, 3e-3, solid)
@@ -278,3 +281,23 @@ def test_autotune_keeps_state():
     ref, _ = gpu_run(19, solid, (1, 1, 1), (1e-5, 0, 0), "f32", 5, state=st, kernel="simple")
     for x, y in zip(a, ref):
         assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("q", (19, 27))
+@pytest.mark.parametrize("storage", ("f64", "f32"))
+def test_channel_t1000_matches_stored_oracle(q, storage):
+    """The 32^3 Poiseuille channel at t = 1000 against the oracle's stored
+    column (tests/golden/channel_t1000.json), on the full 32^3 box."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "channel_t1000.json")) as f:
+        gold = json.load(f)
+    solid = lbm_inputs.channel(32, 32, 32)
+    out, _ = gpu_run(q, solid, (1, 1, 0), (gold["g"], 0, 0), storage, gold["steps"])
+    ref_u = np.array(gold[f"D3Q{q}"]["ux"])
+    ref_d = np.array(gold[f"D3Q{q}"]["drho"])
+    tol = 1e-12 if storage == "f64" else 1e-5
+    umax = np.max(np.abs(ref_u))
+    assert np.max(np.abs(out[1] - ref_u[:, None, None])) <= tol * umax
+    assert np.max(np.abs(out[0] - ref_d[:, None, None])) <= (1e-12 if storage == "f64" else 1e-9)
+    assert np.max(np.abs(out[2])) <= tol * umax and np.max(np.abs(out[3])) <= tol * umax
