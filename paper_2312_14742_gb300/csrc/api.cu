@@ -37,6 +37,10 @@ struct lbm_tau1 {
     float scale_host[8] = {};           // staging for scale copies
     int kernel = LBM_KERNEL_SIMPLE;
     int variant = 0;            // tile-shape variant of the tiled kernel
+    bool sparse = false;        // fluid-list layout: buf holds nf records
+    int64_t nf = 0;             // sparse: fluid nodes in the list
+    int* pos = nullptr;         // sparse: box node of each list entry
+    int* nbr = nullptr;         // sparse: neighbour table [(q-1)][nf]
     int64_t launches = 0;
     std::string err;
 };
@@ -75,6 +79,8 @@ void free_all(lbm_tau1* h)
         if (h->fbuf[b]) cudaFree(h->fbuf[b]);
     }
     if (h->flags) cudaFree(h->flags);
+    if (h->pos) cudaFree(h->pos);
+    if (h->nbr) cudaFree(h->nbr);
     if (h->red_partials) cudaFree(h->red_partials);
     if (h->red_out) cudaFree(h->red_out);
     if (h->red_host) cudaFreeHost(h->red_host);
@@ -196,8 +202,45 @@ lbm_status bgk_from_state(lbm_tau1* h)
     return LBM_OK;
 }
 
+// Sparse layout: numbers the fluid nodes (prefix sum of the flags), then
+// allocates and fills the list records' copies, pos and the neighbour table.
+lbm_status build_fluid_list(lbm_tau1* h)
+{
+    const int nb = sparse_scan_blocks(h->n);
+    int* counts = nullptr;
+    int* idx = nullptr;
+    LBM_CUDA(h, cudaMallocAsync((void**)&counts, (size_t)(nb + 1) * sizeof(int), h->stream), "sparse: scratch");
+    cudaError_t e = launch_sparse_count(h->n, h->flags, counts, h->stream);
+    h->launches += 2;
+    int nf = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&nf, counts + nb, sizeof(int), cudaMemcpyDefault, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) { cudaFreeAsync(counts, h->stream); return cuda_fail(h, e, "sparse: count"); }
+    for (int b = 0; b < 2; ++b)
+        if (h->buf[b]) { cudaFree(h->buf[b]); h->buf[b] = nullptr; }
+    if (h->pos) { cudaFree(h->pos); h->pos = nullptr; }
+    if (h->nbr) { cudaFree(h->nbr); h->nbr = nullptr; }
+    h->nf = nf;
+    const size_t nrec = (size_t)(nf > 0 ? nf : 1);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaMalloc(&h->buf[b], nrec * h->node_bytes);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->pos, nrec * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->nbr, nrec * (size_t)(h->cfg.q - 1) * sizeof(int));
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&idx, (size_t)h->n * sizeof(int), h->stream);
+    if (e == cudaSuccess) {
+        int per[3] = {h->cfg.periodic[0] ? 1 : 0, h->cfg.periodic[1] ? 1 : 0, h->cfg.periodic[2] ? 1 : 0};
+        e = launch_sparse_build(h->cfg.q, h->cfg.nx, h->cfg.ny, h->cfg.nz, per, h->flags, counts, idx, h->pos, nf,
+                                h->nbr, h->stream);
+        h->launches += 2;
+    }
+    if (idx) cudaFreeAsync(idx, h->stream);
+    cudaFreeAsync(counts, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "sparse: fluid list");
+    return LBM_OK;
+}
+
 cudaError_t launch_kernel(const lbm_tau1* h, int variant, const StepArgs& a)
 {
+    if (h->sparse) return launch_tau1_sparse(h->cfg.q, h->cfg.storage, a, (int)h->nf, h->nbr, h->stream);
     if (h->kernel == LBM_KERNEL_TILED) return launch_tau1_tiled(h->cfg.q, h->cfg.storage, variant, a, h->stream);
     return launch_tau1_simple(h->cfg.q, h->cfg.storage, a, h->stream);
 }
@@ -221,8 +264,8 @@ lbm_status launch_step(lbm_tau1* h)
     ++h->step;
     if (h->dscale && h->step % RESCALE_EVERY == 0) {
         const int64_t nb = (rescale_scratch_floats(h->n) - 4) / 4;
-        e = launch_rescale(h->cfg.storage, h->n, h->buf[h->cur], h->flags, h->dscale, h->rescale_scratch,
-                           h->rescale_scratch + 4 * nb, gmax_of(h), h->stream);
+        e = launch_rescale(h->cfg.storage, h->sparse ? h->nf : h->n, h->buf[h->cur], h->sparse ? nullptr : h->flags,
+                           h->dscale, h->rescale_scratch, h->rescale_scratch + 4 * nb, gmax_of(h), h->stream);
         h->launches += 3;
         if (e != cudaSuccess) return cuda_fail(h, e, "rescale kernels");
     }
@@ -267,7 +310,11 @@ lbm_status lbm_tau1_create(const lbm_tau1_config* cfg, lbm_tau1** out)
     if (cfg->q != 19 && cfg->q != 27) return fail(nullptr, LBM_EINVAL, "create: q must be 19 or 27");
     if (storage_node_bytes(cfg->storage) == 0) return fail(nullptr, LBM_EINVAL, "create: bad storage");
     if (cfg->nx < 1 || cfg->ny < 1 || cfg->nz < 1) return fail(nullptr, LBM_EINVAL, "create: box sizes must be >= 1");
-    if (cfg->layout != LBM_DENSE) return fail(nullptr, LBM_EINVAL, "create: only the dense layout is available");
+    if (cfg->layout != LBM_DENSE && cfg->layout != LBM_SPARSE) return fail(nullptr, LBM_EINVAL, "create: bad layout");
+    if (cfg->layout == LBM_SPARSE && cfg->scheme != LBM_SCHEME_TAU1)
+        return fail(nullptr, LBM_EINVAL, "create: the sparse layout is for the Tau1 scheme");
+    if (cfg->layout == LBM_SPARSE && (int64_t)cfg->nx * cfg->ny * cfg->nz >= ((int64_t)1 << 31))
+        return fail(nullptr, LBM_EINVAL, "create: the sparse layout takes boxes of fewer than 2^31 nodes");
     if (cfg->scheme != LBM_SCHEME_TAU1 && cfg->scheme != LBM_SCHEME_BGK)
         return fail(nullptr, LBM_EINVAL, "create: bad scheme");
     if (cfg->scheme == LBM_SCHEME_BGK && !bgk_supported(cfg->q, cfg->storage))
@@ -285,6 +332,8 @@ lbm_status lbm_tau1_create(const lbm_tau1_config* cfg, lbm_tau1** out)
     h->n = n;
     h->node_bytes = storage_node_bytes(cfg->storage);
     h->kernel = cfg->kernel;
+    h->sparse = cfg->layout == LBM_SPARSE;
+    if (h->sparse) h->kernel = LBM_KERNEL_SIMPLE;  // one thread per fluid node; no tile variants
     const bool tiled_ok = tau1_tiled_supported(cfg->q, cfg->storage, n);
     if (h->kernel == LBM_KERNEL_AUTO) h->kernel = tiled_ok ? LBM_KERNEL_TILED : LBM_KERNEL_SIMPLE;
     if (h->kernel == LBM_KERNEL_TILED && !tiled_ok) {
@@ -293,7 +342,8 @@ lbm_status lbm_tau1_create(const lbm_tau1_config* cfg, lbm_tau1** out)
     }
     cudaError_t e = cudaSuccess;
     h->bgk = cfg->scheme == LBM_SCHEME_BGK;
-    for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaMalloc(&h->buf[b], (size_t)n * h->node_bytes);
+    // dense: two copies of the box; sparse: allocated by set_geometry (nf records)
+    for (int b = 0; b < 2 && e == cudaSuccess && !h->sparse; ++b) e = cudaMalloc(&h->buf[b], (size_t)n * h->node_bytes);
     if (h->bgk)
         for (int b = 0; b < 2 && e == cudaSuccess; ++b)
             e = cudaMalloc(&h->fbuf[b], (size_t)n * cfg->q * (cfg->storage == LBM_F64 ? 8 : 4));
@@ -348,12 +398,15 @@ lbm_status lbm_tau1_set_geometry(lbm_tau1* h, const uint8_t* solid, int on_devic
     ++h->launches;
     if (tmp) cudaFreeAsync(tmp, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "set_geometry: flags kernel");
+    if (h->sparse)
+        if (lbm_status st = build_fluid_list(h)) return st;
     const double zero[4] = {0, 0, 0, 0};
     set_scales(h, zero);
     if (lbm_status st = upload_scales(h)) return st;
     for (int b = 0; b < 2; ++b) {
         // drho = 0, u = 0 on fluid nodes; solid nodes marked with drho = NaN
-        e = launch_import_state(h->cfg.storage, h->n, nullptr, h->buf[b], h->flags, h->scale, h->stream);
+        if (h->sparse) e = launch_import_sparse(h->cfg.storage, (int)h->nf, nullptr, h->pos, h->buf[b], h->scale, h->stream);
+        else e = launch_import_state(h->cfg.storage, h->n, nullptr, h->buf[b], h->flags, h->scale, h->stream);
         ++h->launches;
         if (e != cudaSuccess) return cuda_fail(h, e, "set_geometry: state init");
     }
@@ -400,7 +453,10 @@ lbm_status lbm_tau1_set_fields(lbm_tau1* h, const double* drho, const double* ux
         set_scales(h, h->red_host);
         if (lbm_status st = upload_scales(h)) return st;
     }
-    cudaError_t e = launch_import_state(h->cfg.storage, h->n, dsrc, h->buf[h->cur], h->flags, h->scale, h->stream);
+    cudaError_t e = h->sparse
+                        ? launch_import_sparse(h->cfg.storage, (int)h->nf, dsrc, h->pos, h->buf[h->cur], h->scale,
+                                               h->stream)
+                        : launch_import_state(h->cfg.storage, h->n, dsrc, h->buf[h->cur], h->flags, h->scale, h->stream);
     ++h->launches;
     if (tmp) cudaFreeAsync(tmp, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "set_fields: import kernel");
@@ -422,7 +478,16 @@ lbm_status lbm_tau1_get_fields(lbm_tau1* h, double* drho, double* ux, double* uy
     LBM_CUDA(h, cudaMallocAsync((void**)&tmp, 4 * bytes, h->stream), "get_fields: staging allocation");
     double* ddst[4];
     for (int f = 0; f < 4; ++f) ddst[f] = (on_device && dst[f]) ? dst[f] : tmp + f * h->n;
-    cudaError_t e = launch_export_state(h->cfg.storage, h->n, h->buf[h->cur], ddst, h->flags, h->inv_scale, h->stream);
+    cudaError_t e = cudaSuccess;
+    if (h->sparse) {
+        // solid nodes report 0: clear, then scatter the list
+        for (int f = 0; f < 4 && e == cudaSuccess; ++f)
+            if (dst[f] || !on_device) e = cudaMemsetAsync(ddst[f], 0, bytes, h->stream);
+        if (e == cudaSuccess)
+            e = launch_export_sparse(h->cfg.storage, (int)h->nf, h->buf[h->cur], h->pos, ddst, h->inv_scale, h->stream);
+    } else {
+        e = launch_export_state(h->cfg.storage, h->n, h->buf[h->cur], ddst, h->flags, h->inv_scale, h->stream);
+    }
     ++h->launches;
     if (e != cudaSuccess) { cudaFreeAsync(tmp, h->stream); return cuda_fail(h, e, "get_fields: export kernel"); }
     if (!on_device) {
@@ -510,7 +575,8 @@ lbm_status lbm_tau1_reduce(lbm_tau1* h, lbm_tau1_stats* out)
     if (lbm_status st = bgk_refresh_state(h)) return st;
     if (lbm_status st = download_scales(h)) return st;
     const void* f[4] = {h->buf[h->cur], nullptr, nullptr, nullptr};
-    cudaError_t e = launch_reduce(h->cfg.storage, true, h->n, f, h->inv_scale, h->flags, h->cfg.g, h->red_partials,
+    cudaError_t e = launch_reduce(h->cfg.storage, true, h->sparse ? h->nf : h->n, f, h->inv_scale,
+                                  h->sparse ? nullptr : h->flags, h->cfg.g, h->red_partials,
                                   h->red_out, h->stream);
     h->launches += 2;
     if (e != cudaSuccess) return cuda_fail(h, e, "reduce: kernel");

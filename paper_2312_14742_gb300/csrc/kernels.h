@@ -19,6 +19,20 @@ cudaError_t launch_tau1_tiled_tma(int q, int storage, int variant, const StepArg
 // Waits of the staged kernel that ran out (counted on the device since the last call), then reset.
 unsigned int tma_timeouts_take();
 
+// Sparse layout (fluid list + neighbour table). count: counts[0..nb) become
+// the exclusive prefix sums of the fluid counts of the scan blocks and
+// counts[nb] the total; build: idx (n ints) and pos (nf ints), then nbr
+// ((q-1) nf ints). The step reads the list records of a.pre, writes a.post.
+int sparse_scan_blocks(int64_t n);
+cudaError_t launch_sparse_count(int64_t n, const uint8_t* flags, int* counts, cudaStream_t s);
+cudaError_t launch_sparse_build(int q, int nx, int ny, int nz, const int periodic[3], const uint8_t* flags,
+                                const int* offsets, int* idx, int* pos, int nf, int* nbr, cudaStream_t s);
+cudaError_t launch_tau1_sparse(int q, int storage, const StepArgs& a, int nf, const int* nbr, cudaStream_t s);
+cudaError_t launch_import_sparse(int storage, int nf, const double* const src[4], const int* pos, void* dst,
+                                 const float scale[4], cudaStream_t s);
+cudaError_t launch_export_sparse(int storage, int nf, const void* src, const int* pos, double* const dst[4],
+                                 const float inv_scale[4], cudaStream_t s);
+
 // Standard BGK (tau = 1, stored populations) comparison kernels. Populations:
 // [q][n] in the storage type (FP32 or FP64). init: populations from state
 // records; moments: state records from the populations a step would gather.
@@ -52,7 +66,7 @@ cudaError_t launch_absmax_f64(int64_t n, const double* const src[4], const uint8
                               double* scratch, int scratch_blocks, cudaStream_t s);
 
 // FP64 reductions. partials holds reduce_blocks(n) * RED_FIELDS doubles; out
-// receives RED_FIELDS doubles. The state is either one array of records
+// receives RED_FIELDS doubles. flags NULL: every node is fluid (a fluid list). The state is either one array of records
 // (aos = true, fields[0] the base) or four arrays of one field each.
 enum { RED_NFLUID = 0, RED_DRHO, RED_PX, RED_PY, RED_PZ, RED_UMAX, RED_NONFINITE, RED_FIELDS = 8 };
 int reduce_blocks(int64_t n);

@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(RT) reduce_pass1(int64_t n, Fields4 fl, Sc4r i
     const int64_t hi = lo + per < n ? lo + per : n;
     double v[RED_FIELDS] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int64_t i = lo + threadIdx.x; i < hi; i += RT) {
-        if (flags[i] & FLAG_SOLID) continue;
+        if (flags && (flags[i] & FLAG_SOLID)) continue;
         double d, px, py, pz;
         if constexpr (AOS) {
             T v0, v1, v2, v3;

@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(AB) absmax_state_kernel(int64_t n, const void*
     for (int f = 0; f < 4; ++f) inv[f] = dscale[4 + f];
     float m[4] = {0.f, 0.f, 0.f, 0.f};
     for (int64_t i = (int64_t)blockIdx.x * AB + threadIdx.x; i < n; i += (int64_t)gridDim.x * AB) {
-        if (flags[i] & FLAG_SOLID) continue;
+        if (flags && (flags[i] & FLAG_SOLID)) continue;
         float v[4];
         S::load(state, (uint32_t)i, inv, v[0], v[1], v[2], v[3]);
 #pragma unroll

@@ -114,3 +114,10 @@ def test_abi_version_and_cpu_errors(lib):
     assert "q must be" in lbm.lbm_tau1_last_error(None)
     assert lbm.lbm_tau1_step(None, 1) == lbm.LBM_EINVAL
     assert lbm.lbm_tau1_destroy(None) == lbm.LBM_OK
+    # the sparse layout is for the Tau1 scheme; layouts other than dense and sparse are rejected
+    cfg.q, cfg.storage, cfg.layout, cfg.scheme = 19, lbm.LBM_F32, lbm.LBM_SPARSE, lbm.LBM_SCHEME_BGK
+    st, h = lbm.lbm_tau1_create(cfg)
+    assert st == lbm.LBM_EINVAL and "sparse" in lbm.lbm_tau1_last_error(None)
+    cfg.layout, cfg.scheme = 5, lbm.LBM_SCHEME_TAU1
+    st, h = lbm.lbm_tau1_create(cfg)
+    assert st == lbm.LBM_EINVAL and "layout" in lbm.lbm_tau1_last_error(None)
