@@ -180,6 +180,15 @@ lbm_status lbm_tau1_set_variant(lbm_tau1* h, int32_t variant);
  * Errors: LBM_EINVAL (trials < 1), LBM_ESTATE (no geometry), LBM_ECUDA. */
 lbm_status lbm_tau1_autotune(lbm_tau1* h, int32_t trials, int32_t* chosen, float* ms_per_step);
 
+/* Autotune cache for the whole process: path of a JSON file of chosen
+ * variants keyed by device name, lattice, storage, layout, size bucket
+ * (ceil log2 of nx*ny*nz) and whether the box has full tiles. With a cache
+ * set, lbm_tau1_autotune first looks its key up and, when found, selects that
+ * variant without timing (returning the stored ms per step); otherwise it
+ * times the variants and writes its choice to the file. NULL or "" turns the
+ * cache off (the default). The file is read and rewritten on each use. */
+void lbm_tau1_set_tune_cache(const char* path);
+
 /* ---- Batches: many boxes stepped together (continuous batching) ----------
  * No counterpart in the paper, which steps one domain at a time. A batch
  * holds up to `capacity` live boxes of one lattice and storage format, each

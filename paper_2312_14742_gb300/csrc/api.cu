@@ -202,6 +202,25 @@ lbm_status bgk_from_state(lbm_tau1* h)
     return LBM_OK;
 }
 
+// Autotune cache key: device, lattice, storage, layout, size bucket
+// (ceil log2 of the node count) and whether every tile is full (the staged
+// kernel's condition), e.g. "NVIDIA GB300/D3Q19/F32/dense/n2^24/full".
+std::string tune_key(const lbm_tau1* h)
+{
+    int dev = 0;
+    cudaDeviceProp p{};
+    std::string name = "unknown";
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaGetDeviceProperties(&p, dev) == cudaSuccess) name = p.name;
+    static const char* st[] = {"F64", "F32", "F16S", "BF16S"};
+    int lg = 0;
+    while (((int64_t)1 << lg) < h->n) ++lg;
+    const bool full = h->cfg.nx % 32 == 0 && h->cfg.ny % 16 == 0;
+    char buf[256];
+    std::snprintf(buf, sizeof(buf), "%s/D3Q%d/%s/%s/n2^%d/%s", name.c_str(), h->cfg.q, st[h->cfg.storage],
+                  h->sparse ? "sparse" : "dense", lg, full ? "full" : "ragged");
+    return buf;
+}
+
 // Sparse layout: numbers the fluid nodes (prefix sum of the flags), then
 // allocates and fills the list records' copies, pos and the neighbour table.
 lbm_status build_fluid_list(lbm_tau1* h)
@@ -532,6 +551,15 @@ lbm_status lbm_tau1_autotune(lbm_tau1* h, int32_t trials, int32_t* chosen, float
         if (ms_per_step) *ms_per_step = 0.f;
         return LBM_OK;
     }
+    const std::string key = tune_key(h);
+    int cached = 0;
+    double cached_ms = 0;
+    if (tune_cache_lookup(key, &cached, &cached_ms) && cached >= 0 && cached < variant_count(h)) {
+        h->variant = cached;
+        if (chosen) *chosen = cached;
+        if (ms_per_step) *ms_per_step = (float)cached_ms;
+        return LBM_OK;
+    }
     // Every trial launch reads the current copy and rewrites the other one
     // without swapping, so the state is left as it was.
     StepArgs a;
@@ -564,8 +592,11 @@ lbm_status lbm_tau1_autotune(lbm_tau1* h, int32_t trials, int32_t* chosen, float
     h->variant = best;
     if (chosen) *chosen = best;
     if (ms_per_step) *ms_per_step = best_ms;
+    tune_cache_store(key, best, best_ms);
     return LBM_OK;
 }
+
+void lbm_tau1_set_tune_cache(const char* path) { tune_cache_set_path(path); }
 
 lbm_status lbm_tau1_reduce(lbm_tau1* h, lbm_tau1_stats* out)
 {

@@ -2,7 +2,10 @@
 // one step in one launch.
 //
 // The work of a step is the list of tile columns of every live box (box-major,
-// each box chunk-major as in the single-box kernel). A grid of (SMs x resident
+// each box chunk-major as in the single-box kernel). Columns are `chunk`
+// planes high; the host lowers the chunk (32 down to 4 planes) when few boxes
+// are live, so that a step spreads over the SMs and its latency, one column,
+// stays short. A node's result does not depend on the chunk. A grid of (SMs x resident
 // blocks) walks the list; each item is one tile_column() call with that box's
 // arguments, read from the device table. Everything that changes from step to
 // step lives in the table on the device: which copy holds a box's current
@@ -71,7 +74,7 @@ __global__ void __launch_bounds__(32 * H, MINB) tau1_batch_kernel(BatchTable* T)
     extern __shared__ __align__(32) unsigned char smem_raw[];
     __shared__ int last;
     constexpr bool AMAX = ST == ST_F16S || ST == ST_BF16S;
-    const int nitems = T->nitems, ndom = T->ndom;
+    const int nitems = T->nitems, ndom = T->ndom, chunk = T->chunk;
     const int* __restrict__ begin = T->item_begin;
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         // box of this item: the last d with begin[d] <= it
@@ -90,8 +93,8 @@ __global__ void __launch_bounds__(32 * H, MINB) tau1_batch_kernel(BatchTable* T)
         a.seed = step_seed(R.step);
         const Scales sc(AMAX ? R.scale[c] : nullptr, AMAX ? R.scale[c ^ 1] : nullptr);
         const int tile = local % R.ntiles;
-        const int z0 = (local / R.ntiles) * R.chunk;
-        const int z1 = min(a.nz, z0 + R.chunk);
+        const int z0 = (local / R.ntiles) * chunk;
+        const int z1 = min(a.nz, z0 + chunk);
         const int x0 = (tile % R.ntx) * 32, y0 = (tile / R.ntx) * (2 * H);
         float amax[4] = {0.f, 0.f, 0.f, 0.f};
         __syncthreads();  // the previous item's last shared-memory reads are done

@@ -13,7 +13,7 @@ constexpr int BATCH_RESCALE_EVERY = 64;  // FP16 storage: steps between scale ch
 struct BatchDomain {
     StepArgs a;          // sizes, periodicity, g (pre, post, dscale, seed unused)
     void* buf[2];        // ping-pong state records
-    int ntx, ntiles, chunk, items;  // tile columns: ntiles per chunk, items in all
+    int ntx, ntiles;     // tiles in x, tiles per plane
     uint32_t cur;        // buf[cur] holds the current state
     int64_t step;        // steps taken
     float scale[2][8];   // 16-bit: {S, 1/S} of the contents of buf[0], buf[1]
@@ -26,7 +26,7 @@ struct BatchTable {
     int nitems;              // work items (tile columns) of all live boxes
     int ndom;                // live boxes
     unsigned done;           // blocks finished in the current step
-    int pad;
+    int chunk;               // planes per work item (the same for every box)
     const int* live;         // [ndom] slot of each live box
     const int* item_begin;   // [ndom] first item of each live box
     BatchDomain* dom;        // [capacity] by slot

@@ -37,7 +37,7 @@ struct Slot {
     uint8_t* flags = nullptr;
     uint64_t bytes = 0;
     int64_t steps = 0;
-    int items = 0;
+    int ntiles = 0;  // tiles per plane
 };
 
 uint64_t round256(uint64_t b) { return (b + 255) & ~(uint64_t)255; }
@@ -119,22 +119,35 @@ cudaError_t stage_done(Stage* s, cudaStream_t stream)
     return e;
 }
 
-// Rebuilds the live list and item offsets and queues their upload.
+// Work items of a box for a chunk height.
+int box_items(const Slot& s, int chunk) { return s.ntiles * ((s.cfg.nz + chunk - 1) / chunk); }
+
+// Rebuilds the live list and item offsets and queues their upload. The chunk
+// is the tallest of 32, 16, 8 planes that still gives at least two items per
+// block of the persistent grid, else 4.
 lbm_status upload_table(lbm_tau1_batch* b)
 {
+    int chunk = 32;
+    for (; chunk > 4; chunk /= 2) {
+        int64_t tot = 0;
+        for (const Slot& s : b->slots)
+            if (s.live) tot += box_items(s, chunk);
+        if (tot >= 2 * (int64_t)b->grid) break;
+    }
     std::vector<int> live, begin;
     int items = 0;
     for (int i = 0; i < (int)b->slots.size(); ++i)
         if (b->slots[i].live) {
             live.push_back(i);
             begin.push_back(items);
-            items += b->slots[i].items;
+            items += box_items(b->slots[i], chunk);
         }
     const int nd = (int)live.size();
     BatchTable hdr{};
     hdr.nitems = items;
     hdr.ndom = nd;
     hdr.done = 0;
+    hdr.chunk = chunk;
     hdr.live = b->dlive;
     hdr.item_begin = b->dbegin;
     hdr.dom = b->ddom;
@@ -363,9 +376,6 @@ lbm_status lbm_tau1_batch_admit(lbm_tau1_batch* b, const lbm_tau1_config* cfg, c
     rec.ntx = (cfg->nx + 31) / 32;
     const int nty = (cfg->ny + b->tile_h - 1) / b->tile_h;
     rec.ntiles = rec.ntx * nty;
-    rec.chunk = cfg->nz < 32 ? cfg->nz : 32;
-    const int nchunks = (cfg->nz + rec.chunk - 1) / rec.chunk;
-    rec.items = rec.ntiles * nchunks;
     rec.cur = 0;
     rec.step = 0;
     for (int c = 0; c < 2; ++c)
@@ -387,7 +397,7 @@ lbm_status lbm_tau1_batch_admit(lbm_tau1_batch* b, const lbm_tau1_config* cfg, c
     s.n = n;
     s.bytes = need;
     s.steps = 0;
-    s.items = rec.items;
+    s.ntiles = rec.ntiles;
     b->used += need;
     if (lbm_status r = upload_table(b)) return r;
     *slot = id;

@@ -3,9 +3,9 @@
 // tensor unit (cp.async.bulk.tensor), two planes ahead of its use, instead of
 // per-thread global loads held in registers across the plane barrier.
 //
-// It serves boxes whose tiles are all full (nx a multiple of 32, ny of the
-// tile height) so that every tile lies inside the box; halo nodes across a
-// periodic face, which the box copy cannot wrap, are read from global memory.
+// Box parts outside the state (a ragged last tile, the halo across a face)
+// come back zero-filled from the copy; those nodes are read from global memory
+// (periodic images, which the copy cannot wrap) or are walls.
 // The state is viewed as a 3D array of 4 nx x ny x nz values (one record is
 // 4 values), so that a box row of 34 records starts at an element coordinate
 // that is a multiple of 4 values: a multiple of 16 bytes for every format.
@@ -85,8 +85,8 @@ cudaError_t launch_t(const StepArgs& a, cudaStream_t s)
     CUtensorMap map;
     cudaError_t e = encode_state<ST>(&map, a, 2 * H + 2);
     if (e != cudaSuccess) return e;
-    const int ntx = a.nx / 32;
-    const int ntiles = ntx * (a.ny / (2 * H));
+    const int ntx = (a.nx + 31) / 32;
+    const int ntiles = ntx * ((a.ny + 2 * H - 1) / (2 * H));
     const int chunk = a.nz < 32 ? a.nz : 32;
     const int nchunks = (a.nz + chunk - 1) / chunk;
     const long long blocks = (long long)ntiles * nchunks;
@@ -115,8 +115,9 @@ cudaError_t launch_v(int variant, const StepArgs& a, cudaStream_t s)
 
 bool tau1_tiled_tma_ok(int q, int storage, int variant, const StepArgs& a)
 {
-    const int th = tile_height(q, storage, variant);
-    if (th == 0 || a.nx % 32 != 0 || a.ny % th != 0) return false;
+    if (tile_height(q, storage, variant) == 0) return false;
+    // a box row of 16-bit records starts at a multiple of 16 bytes only if nx is even
+    if ((storage == ST_F16S || storage == ST_BF16S) && a.nx % 2 != 0) return false;
     if ((reinterpret_cast<uintptr_t>(a.pre) & 15) != 0) return false;
     return encode_fn() != nullptr;
 }

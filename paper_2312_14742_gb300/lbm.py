@@ -76,6 +76,7 @@ SIGNATURES = {
     "lbm_tau1_variant_count": (ctypes.c_int32, [_H]),
     "lbm_tau1_set_variant": (_I, [_H, ctypes.c_int32]),
     "lbm_tau1_autotune": (_I, [_H, ctypes.c_int32, _P, _P]),
+    "lbm_tau1_set_tune_cache": (None, [ctypes.c_char_p]),
     "lbm_tau1_batch_create": (_I, [ctypes.POINTER(lbm_tau1_batch_config), ctypes.POINTER(_H)]),
     "lbm_tau1_batch_footprint": (ctypes.c_uint64, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
     "lbm_tau1_batch_admit": (_I, [_H, ctypes.POINTER(lbm_tau1_config), _P, _I, ctypes.POINTER(ctypes.c_int32)]),
@@ -183,6 +184,10 @@ def lbm_tau1_set_variant(h, variant: int) -> int:
 
 def lbm_tau1_autotune(h, trials: int, chosen=None, ms_per_step=None) -> int:
     return _fn("lbm_tau1_autotune")(h, trials, chosen, ms_per_step)
+
+
+def lbm_tau1_set_tune_cache(path) -> None:
+    _fn("lbm_tau1_set_tune_cache")(None if path is None else os.fsencode(path))
 
 
 def lbm_tau1_reduce_noalloc(storage, n, drho, ux, uy, uz, inv_scale, solid, g, out, stream) -> int:

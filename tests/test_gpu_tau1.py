@@ -301,3 +301,34 @@ def test_channel_t1000_matches_stored_oracle(q, storage):
     assert np.max(np.abs(out[1] - ref_u[:, None, None])) <= tol * umax
     assert np.max(np.abs(out[0] - ref_d[:, None, None])) <= (1e-12 if storage == "f64" else 1e-9)
     assert np.max(np.abs(out[2])) <= tol * umax and np.max(np.abs(out[3])) <= tol * umax
+
+
+def test_autotune_cache(tmp_path):
+    """With a cache file set, the first autotune times the variants and
+    records its choice; a later handle with the same key takes it from the
+    file without launching trials. Entries of other keys are kept."""
+    import json
+    from paper_2312_14742_gb300 import lbm
+    path = tmp_path / "tune.json"
+    lbm.lbm_tau1_set_tune_cache(str(path))
+    try:
+        solid, _ = lbm_inputs.sphere_pack(64, 48, 40, 4.0, 0.8, 5150)
+        nz, ny, nx = solid.shape
+        with Tau1(19, (nx, ny, nz), storage="f32", g=(1e-5, 0, 0)) as t:
+            t.set_geometry(solid)
+            v, ms = t.autotune(3)
+        entries = json.loads(path.read_text())["entries"]
+        (key, rec), = entries.items()
+        assert "/D3Q19/F32/dense/n2^17/full" in key and rec["variant"] == v
+        with Tau1(19, (nx, ny, nz), storage="f32", g=(1e-5, 0, 0)) as t:
+            t.set_geometry(solid)
+            n0 = t.launch_count
+            v2, ms2 = t.autotune(3)
+            assert t.launch_count == n0 and v2 == v and ms2 == pytest.approx(rec["ms_per_step"], rel=1e-5)
+        with Tau1(27, (nx, ny, nz), storage="f32", g=(1e-5, 0, 0)) as t:
+            t.set_geometry(solid)
+            t.autotune(2)
+        entries = json.loads(path.read_text())["entries"]
+        assert len(entries) == 2 and entries[key]["variant"] == v
+    finally:
+        lbm.lbm_tau1_set_tune_cache(None)
