@@ -19,7 +19,7 @@
 // that both sources x - c_k of a thread sit at one pair position
 // (x - c_x, y - c_y). Pair row -1 holds the halo row below (A) and interior
 // row H-1 (B); pair row H holds interior row H (A) and the halo row above
-// (B). Warp 0 computes both halo rows as one two-lane pair, warp 1 the two
+// (B). Warp 2 (warp 0 when H < 3) computes both halo rows as one two-lane pair, warp 1 the two
 // halo columns; the owners of rows H-1 and H copy their exports into pair
 // rows -1 and H. Halo nodes export only the directions pointing into the tile.
 //
@@ -224,9 +224,9 @@ __device__ __forceinline__ void tile_column(const StepArgs& a, const Scales& sc,
     bool okA, okB;
     const uint32_t xyA = xy_of(gx, gyA, okA), xyB = xy_of(gx, gyB, okB);
 
-    // halo roles. Warp 0: halo rows below (lane A) and above (lane B).
+    // halo roles. Warp 2 (warp 0 if H < 3): halo rows below (lane A) and above (lane B).
     // Warp 1: halo columns, lanes 0..H+1 left (x = -1), H+2..2H+3 right (x = 32).
-    const bool hrow = ty == 0;
+    const bool hrow = ty == (H >= 3 ? 2 : 0);  // not warp 0, which also stores a duplicated row
     const bool hcol = ty == 1 && tx < 2 * (H + 2);
     const int hcs = tx < H + 2 ? 1 : -1;  // column ring exports directions with dx = hcs
     const int hctx = tx < H + 2 ? -1 : TX;
