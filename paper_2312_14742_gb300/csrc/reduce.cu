@@ -7,7 +7,8 @@
 // on n, so repeated calls give identical bits.
 //
 // Per fluid node: count, drho, physical velocity u + g/2 (three sums), the
-// max of |u + g/2|, and a count of non-finite values.
+// max of |u + g/2| (kept squared until the last pass), and a count of
+// non-finite values.
 #include "kernels.h"
 
 namespace lbm {
@@ -115,7 +116,9 @@ __global__ void __launch_bounds__(RT) reduce_pass1(int64_t n, Fields4 fl, Sc4r i
         v[RED_PX] += px;
         v[RED_PY] += py;
         v[RED_PZ] += pz;
-        const double m = sqrt(px * px + py * py + pz * pz);
+        // squared magnitude here; one square root of the maximum at the end
+        // (sqrt is monotone and correctly rounded: the same value as the max of roots)
+        const double m = px * px + py * py + pz * pz;
         if (isfinite(d) && isfinite(m)) v[RED_UMAX] = fmax(v[RED_UMAX], m);
         else v[RED_NONFINITE] += 1.0;
     }
@@ -133,7 +136,7 @@ __global__ void __launch_bounds__(RT) reduce_pass2(int blocks, const double* __r
     block_reduce(v, sm);
     if (threadIdx.x == 0)
 #pragma unroll
-        for (int f = 0; f < RED_FIELDS; ++f) out[f] = v[f];
+        for (int f = 0; f < RED_FIELDS; ++f) out[f] = f == RED_UMAX ? sqrt(v[f]) : v[f];
 }
 
 cudaError_t launch_reduce(int storage, bool aos, int64_t n, const void* const fields[4], const float inv_scale[4],
