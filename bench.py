@@ -174,6 +174,16 @@ def ncu_traffic(args):
     return d.get("dram_bytes_per_launch")
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest x over all ranks (the job's time is its slowest rank's)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def cpu_baseline(args, solid, nsteps):
     import oracle
     D = oracle.Domain(args.q, solid, periodic=(1, 1, 1), g=(args.gx, 0, 0))
@@ -267,11 +277,7 @@ def run_ours(args):
             barrier()
             times.append(e0.elapsed_time(e1) / 1e3)
     launches = (t.launch_count - launches0) // max(1, args.reps)
-    dt = statistics.median(times)
-    if dist is not None:
-        tt = torch.tensor([dt], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        dt = float(tt.item())
+    dt = max_over_ranks(statistics.median(times), dist, dev)
     stats = t.reduce(allow_diverged=True)
 
     # end-to-end through the C ABI with host buffers: geometry in, K steps, fields out
@@ -286,11 +292,7 @@ def run_ours(args):
         st |= L.lbm_tau1_step(t.h, args.steps)
         st |= L.lbm_tau1_get_fields(t.h, *[o.data_ptr() for o in outs], 0)
         barrier()
-        e2e_dt = time.perf_counter() - h0
-        if dist is not None:
-            tt = torch.tensor([e2e_dt], device=dev, dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e2e_dt = float(tt.item())
+        e2e_dt = max_over_ranks(time.perf_counter() - h0, dist, dev)
         if st == 0:
             e2e = {"value": world * nf * args.steps / e2e_dt / 1e9, "unit": "GFLUPS",
                    "h2d_bytes_per_step": n / args.steps, "d2h_bytes_per_step": 4 * 8 * n / args.steps,
