@@ -10,7 +10,10 @@
 // arguments, read from the device table. Everything that changes from step to
 // step lives in the table on the device: which copy holds a box's current
 // state, its step count (the stochastic-rounding seed), its 16-bit scales.
-// A launch therefore has the same arguments every step, and K steps can be
+// Boxes whose tiles are all full are stepped by the staged (TMA) tile column
+// through their own tensor maps (one per state copy, in device memory); the
+// stage mbarriers are set up once per launch and their phases run on from
+// item to item. A launch therefore has the same arguments every step, and K steps can be
 // captured once in a CUDA graph and replayed while boxes come and go (the
 // host edits the table between replays).
 //
@@ -71,11 +74,13 @@ __device__ void finish_box(BatchDomain& R, int storage)
 template <int Q, int ST, int H, int MINB>
 __global__ void __launch_bounds__(32 * H, MINB) tau1_batch_kernel(BatchTable* T)
 {
-    extern __shared__ __align__(32) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ int last;
     constexpr bool AMAX = ST == ST_F16S || ST == ST_BF16S;
     const int nitems = T->nitems, ndom = T->ndom, chunk = T->chunk;
     const int* __restrict__ begin = T->item_begin;
+    stage_init<Q, ST, H>(smem_raw);  // visible after the first item's barrier
+    uint32_t phase = 0;
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         // box of this item: the last d with begin[d] <= it
         int lo = 0, hi = ndom - 1;
@@ -84,7 +89,8 @@ __global__ void __launch_bounds__(32 * H, MINB) tau1_batch_kernel(BatchTable* T)
             if (begin[mid] <= it) lo = mid;
             else hi = mid - 1;
         }
-        BatchDomain& R = T->dom[T->live[lo]];
+        const int slot = T->live[lo];
+        BatchDomain& R = T->dom[slot];
         const int local = it - begin[lo];
         StepArgs a = R.a;
         const uint32_t c = R.cur;
@@ -98,7 +104,10 @@ __global__ void __launch_bounds__(32 * H, MINB) tau1_batch_kernel(BatchTable* T)
         const int x0 = (tile % R.ntx) * 32, y0 = (tile / R.ntx) * (2 * H);
         float amax[4] = {0.f, 0.f, 0.f, 0.f};
         __syncthreads();  // the previous item's last shared-memory reads are done
-        tile_column<Q, ST, H, AMAX>(a, sc, x0, y0, z0, z1, smem_raw, amax);
+        if (R.tma)
+            tile_column<Q, ST, H, AMAX, true>(a, sc, x0, y0, z0, z1, smem_raw, amax, T->maps + 2 * slot + c, &phase);
+        else
+            tile_column<Q, ST, H, AMAX, false>(a, sc, x0, y0, z0, z1, smem_raw, amax);
         if constexpr (AMAX) {
 #pragma unroll
             for (int f = 0; f < 4; ++f) {
@@ -127,16 +136,17 @@ struct BatchKernel {
     using E = typename Storage<ST>::ctype;
     static constexpr int H = Shape<Q, E, V>::H;
     using C = TCfg<Q, 32, H, E>;
+    static constexpr size_t SMEM = tile_smem<Q, ST, H, true>();
     static constexpr auto fn() { return tau1_batch_kernel<Q, ST, H, Shape<Q, E, V>::MINB>; }
     static cudaError_t prepare(int& grid, int& tile_h)
     {
         auto kern = fn();
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
         if (e != cudaSuccess) return e;
         int dev = 0, sms = 0, per_sm = 0;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
         if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, C::NT, C::SMEM)) != cudaSuccess)
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, C::NT, SMEM)) != cudaSuccess)
             return e;
         grid = sms * (per_sm > 0 ? per_sm : 1);
         tile_h = 2 * H;
@@ -144,7 +154,7 @@ struct BatchKernel {
     }
     static cudaError_t launch(BatchTable* T, int grid, cudaStream_t s)
     {
-        fn()<<<grid, C::NT, C::SMEM, s>>>(T);
+        fn()<<<grid, C::NT, SMEM, s>>>(T);
         return cudaGetLastError();
     }
 };

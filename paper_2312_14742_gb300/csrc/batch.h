@@ -19,6 +19,7 @@ struct BatchDomain {
     float scale[2][8];   // 16-bit: {S, 1/S} of the contents of buf[0], buf[1]
     unsigned amax[4];    // 16-bit: max |value| stored this step (float bits)
     float gfloor;        // 64 |g|_max, the floor of the headroom rule
+    int tma;             // 1: full tiles, stepped by the staged (TMA) tile column
 };
 
 // Header of a batch in device memory; the step kernel's only argument.
@@ -30,6 +31,7 @@ struct BatchTable {
     const int* live;         // [ndom] slot of each live box
     const int* item_begin;   // [ndom] first item of each live box
     BatchDomain* dom;        // [capacity] by slot
+    const CUtensorMap* maps; // [capacity][2] tensor maps of buf[0], buf[1] (boxes with tma)
 };
 
 // Persistent grid size and tile height (2H) of a kernel variant.

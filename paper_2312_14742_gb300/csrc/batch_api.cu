@@ -55,6 +55,7 @@ struct lbm_tau1_batch {
     BatchDomain* ddom = nullptr;
     int* dlive = nullptr;
     int* dbegin = nullptr;
+    CUtensorMap* dmaps = nullptr;  // [capacity][2]
     Stage ring[RING];
     int ring_pos = 0;
     int grid = 0, tile_h = 0;
@@ -151,6 +152,7 @@ lbm_status upload_table(lbm_tau1_batch* b)
     hdr.live = b->dlive;
     hdr.item_begin = b->dbegin;
     hdr.dom = b->ddom;
+    hdr.maps = b->dmaps;
     const size_t lb = (size_t)nd * sizeof(int);
     Stage* s = nullptr;
     BCUDA(b, stage_get(b, sizeof(hdr) + 2 * lb + 16, &s), "batch: staging buffer");
@@ -214,6 +216,7 @@ void free_batch(lbm_tau1_batch* b)
     if (b->ddom) cudaFree(b->ddom);
     if (b->dlive) cudaFree(b->dlive);
     if (b->dbegin) cudaFree(b->dbegin);
+    if (b->dmaps) cudaFree(b->dmaps);
     if (b->red_partials) cudaFree(b->red_partials);
     if (b->red_out) cudaFree(b->red_out);
     if (b->red_host) cudaFreeHost(b->red_host);
@@ -277,6 +280,7 @@ lbm_status lbm_tau1_batch_create(const lbm_tau1_batch_config* cfg, lbm_tau1_batc
     if (e == cudaSuccess) e = cudaMalloc(&b->ddom, (size_t)cap * sizeof(BatchDomain));
     if (e == cudaSuccess) e = cudaMalloc(&b->dlive, (size_t)cap * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&b->dbegin, (size_t)cap * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&b->dmaps, (size_t)cap * 2 * sizeof(CUtensorMap));
     if (e == cudaSuccess) e = cudaMalloc(&b->red_partials, (size_t)1024 * RED_FIELDS * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&b->red_out, (size_t)cap * RED_FIELDS * sizeof(double));
     if (e == cudaSuccess) e = cudaMallocHost(&b->red_host, (size_t)cap * RED_FIELDS * sizeof(double));
@@ -384,11 +388,24 @@ lbm_status lbm_tau1_batch_admit(lbm_tau1_batch* b, const lbm_tau1_config* cfg, c
             rec.scale[c][4 + f] = 1.0f / sc[f];
         }
     rec.gfloor = (float)(64.0 * gmax);
+    // staged tile columns for boxes of full tiles (16-bit rows start on 16 bytes only for even nx)
+    CUtensorMap maps[2];
+    rec.tma = cfg->nx % 32 == 0 && cfg->ny % b->tile_h == 0 &&
+              !((cfg->storage == LBM_F16S || cfg->storage == LBM_BF16S) && cfg->nx % 2 != 0);
+    for (int c = 0; c < 2 && rec.tma; ++c)
+        if (encode_state_map(cfg->storage, s.buf[c], cfg->nx, cfg->ny, cfg->nz, b->tile_h + 2, &maps[c]) !=
+            cudaSuccess)
+            rec.tma = 0;
     Stage* st = nullptr;
-    BCUDA(b, stage_get(b, sizeof(rec), &st), "batch_admit: staging buffer");
-    std::memcpy(st->p, &rec, sizeof(rec));
+    BCUDA(b, stage_get(b, sizeof(rec) + sizeof(maps), &st), "batch_admit: staging buffer");
+    std::memcpy(st->p, maps, sizeof(maps));
+    std::memcpy(static_cast<unsigned char*>(st->p) + sizeof(maps), &rec, sizeof(rec));
     BCUDA(b, cudaStreamWaitEvent(b->stream, b->side_done, 0), "batch_admit: wait");
-    BCUDA(b, cudaMemcpyAsync(b->ddom + id, st->p, sizeof(rec), cudaMemcpyHostToDevice, b->stream),
+    if (rec.tma)
+        BCUDA(b, cudaMemcpyAsync(b->dmaps + 2 * id, st->p, sizeof(maps), cudaMemcpyHostToDevice, b->stream),
+              "batch_admit: tensor map copy");
+    BCUDA(b, cudaMemcpyAsync(b->ddom + id, static_cast<unsigned char*>(st->p) + sizeof(maps), sizeof(rec),
+                             cudaMemcpyHostToDevice, b->stream),
           "batch_admit: record copy");
     BCUDA(b, stage_done(st, b->stream), "batch_admit: staging event");
 

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -16,6 +17,9 @@ int tau1_tiled_variants(int q, int storage);
 // Staged (TMA) form of the tiled kernel: same bits; for boxes with full tiles.
 bool tau1_tiled_tma_ok(int q, int storage, int variant, const StepArgs& a);
 cudaError_t launch_tau1_tiled_tma(int q, int storage, int variant, const StepArgs& a, cudaStream_t s);
+// Tensor map of a state copy for the staged kernels: 3D {4 nx, ny, nz} values,
+// box {4 (32 + 2 XOFF), box_rows, 1}.
+cudaError_t encode_state_map(int storage, const void* base, int nx, int ny, int nz, int box_rows, CUtensorMap* map);
 // Waits of the staged kernel that ran out (counted on the device since the last call), then reset.
 unsigned int tma_timeouts_take();
 

@@ -33,7 +33,10 @@ __global__ void __launch_bounds__(32 * H, MINB)
     const int x0 = (tile % ntx) * 32, y0 = (tile / ntx) * (2 * H);
     const Scales sc(a.dscale);
     float amax[4];
-    tile_column<Q, ST, H, false, true>(a, sc, x0, y0, z0, z1, smem_raw, amax, &tmap);
+    stage_init<Q, ST, H>(smem_raw);
+    __syncthreads();
+    uint32_t phase = 0;
+    tile_column<Q, ST, H, false, true>(a, sc, x0, y0, z0, z1, smem_raw, amax, &tmap, &phase);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
@@ -69,6 +72,16 @@ template <int ST> cudaError_t encode_state(CUtensorMap* map, const StepArgs& a, 
                           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+template <int ST> cudaError_t encode_at(CUtensorMap* map, const void* base, int nx, int ny, int nz, int box_rows)
+{
+    StepArgs a{};
+    a.nx = nx;
+    a.ny = ny;
+    a.nz = nz;
+    a.pre = base;
+    return encode_state<ST>(map, a, box_rows);
 }
 
 template <int Q, int ST, int V>
@@ -137,6 +150,17 @@ cudaError_t launch_tau1_tiled_tma(int q, int storage, int variant, const StepArg
     case 270 + ST_F32: return launch_v<27, ST_F32>(variant, a, s);
     case 270 + ST_F16S: return launch_v<27, ST_F16S>(variant, a, s);
     case 270 + ST_BF16S: return launch_v<27, ST_BF16S>(variant, a, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t encode_state_map(int storage, const void* base, int nx, int ny, int nz, int box_rows, CUtensorMap* map)
+{
+    switch (storage) {
+    case ST_F64: return encode_at<ST_F64>(map, base, nx, ny, nz, box_rows);
+    case ST_F32: return encode_at<ST_F32>(map, base, nx, ny, nz, box_rows);
+    case ST_F16S: return encode_at<ST_F16S>(map, base, nx, ny, nz, box_rows);
+    case ST_BF16S: return encode_at<ST_BF16S>(map, base, nx, ny, nz, box_rows);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -24,12 +24,15 @@
 // rows -1 and H. Halo nodes export only the directions pointing into the tile.
 //
 // At the "arrival" of plane p every position stores, per in-plane direction
-// (dx, dy) != 0, its values for c_z = -1, 0, +1 and its solid fraction
-// sigma (1 for a solid node or a position beyond a non-periodic face, else
-// 0). Solid nodes export 0. After one barrier each thread gathers: c_z = -1
-// values complete destination plane p - 1, c_z = 0 values go into plane p,
-// c_z = +1 values wait one arrival in registers; (0,0,+-1) and rest never
-// leave the thread. Walls (Algorithm "Complete Tau1 ... halfway
+// (dx, dy) != 0, its values for c_z = -1 and 0 of plane p, its c_z = +1 value
+// of plane p - 1, and its solid fraction sigma of planes p - 1 and p (1 for a
+// solid node or a position beyond a non-periodic face, else 0). Solid nodes
+// export 0. After one barrier each thread gathers: c_z = -1 values complete
+// destination plane p - 1; the c_z = +1 values of plane p - 1 and the c_z = 0
+// values of plane p go into plane p; (0,0,+-1) and rest never leave the
+// thread. A node keeps its own c_z = +1 values one plane for its bounce-back
+// anyway, so exporting them one plane late costs no register, while the
+// receivers carry nothing across the plane loop. Walls (Algorithm "Complete Tau1 ... halfway
 // bounce-back") enter every link as fma(sigma, b, v), where v is the
 // gathered value and b the destination node's own outgoing value in
 // direction inv(k): v for a fluid source, b for a wall, with no branch.
@@ -90,12 +93,13 @@ template <int Q, int TX, int H, typename E> struct TCfg {
     static constexpr int PW = TX + 2;
     static constexpr int NPP = (TX + 2) * (H + 2);  // pair positions
     static constexpr int NT = TX * H;
-    // slot: L01[NB][NPP] {c_z=-1: A, B; c_z=0: A, B} | L2[NB][NPP] {c_z=+1: A, B}
-    //       | DG[ND][NPP] {A, B} | SG[NPP] {sigma A, sigma B}
+    // slot of plane p: L01[NB][NPP] {c_z=-1: A, B; c_z=0: A, B} | L2[NB][NPP]
+    //       {c_z=+1 of plane p-1: A, B} | DG[ND][NPP] {A, B}
+    //       | SG[NPP][2] {sigma of plane p-1: A, B}, {sigma of plane p: A, B}
     static constexpr size_t L01_BYTES = (size_t)NB * NPP * sizeof(V4<E>);
     static constexpr size_t L2_BYTES = (size_t)NB * NPP * sizeof(V2<E>);
     static constexpr size_t DG_BYTES = (size_t)ND * NPP * sizeof(V2<E>);
-    static constexpr size_t SG_BYTES = (size_t)NPP * sizeof(V2<E>);
+    static constexpr size_t SG_BYTES = (size_t)NPP * 2 * sizeof(V2<E>);
     static constexpr size_t SLOT_BYTES = L01_BYTES + L2_BYTES + DG_BYTES + SG_BYTES;
     static constexpr size_t SMEM = 2 * SLOT_BYTES;
     static_assert(TX == 32, "a warp is one tile row");
@@ -125,6 +129,31 @@ template <int Q, int ST, int H, bool TMA> __host__ __device__ constexpr size_t t
     using C = TCfg<Q, 32, H, typename Storage<ST>::ctype>;
     using SC = StageCfg<ST, H>;
     return TMA ? C::SMEM + 128 + SC::NSTAGE * SC::STAGE_BYTES + 8 * SC::NSTAGE : C::SMEM;
+}
+
+// Stage buffers and their mbarriers inside tile_column's shared memory.
+template <int Q, int ST, int H> __device__ __forceinline__ unsigned char* stage_base(unsigned char* smem_raw)
+{
+    using C = TCfg<Q, 32, H, typename Storage<ST>::ctype>;
+    const uint32_t sbase = smem_u32(smem_raw);
+    return smem_raw + (((sbase + (uint32_t)C::SMEM + 127u) & ~127u) - sbase);
+}
+template <int Q, int ST, int H> __device__ __forceinline__ uint64_t* stage_barriers(unsigned char* smem_raw)
+{
+    using SC = StageCfg<ST, H>;
+    return reinterpret_cast<uint64_t*>(stage_base<Q, ST, H>(smem_raw) + SC::NSTAGE * SC::STAGE_BYTES);
+}
+// Initialises the stage mbarriers (thread 0; the caller synchronises the block
+// before the first tile_column). Their phases then run on across calls: each
+// call takes and returns the phase bits.
+template <int Q, int ST, int H> __device__ __forceinline__ void stage_init(unsigned char* smem_raw)
+{
+    if (threadIdx.x == 0) {
+        uint64_t* mbar = stage_barriers<Q, ST, H>(smem_raw);
+#pragma unroll
+        for (int st = 0; st < StageCfg<ST, H>::NSTAGE; ++st) mbar_init(&mbar[st], 1);
+        mbar_init_fence();
+    }
 }
 
 __device__ __forceinline__ int ppos(int tx, int ty, int pw) { return (ty + 1) * pw + (tx + 1); }
@@ -187,13 +216,14 @@ __device__ __forceinline__ void track_amax(float (&m)[4], E d, E ux, E uy, E uz)
 // smem_raw holds tile_smem<Q, ST, H, TMA>() bytes, 128-byte aligned. With
 // AMAX, amax[f] collects the largest |value| of field f among the nodes this
 // thread stores. With TMA the raw records come from shared-memory stages
-// filled by the tensor unit through tmap (the state read, viewed as a 3D
+// (initialised by stage_init; *phase_io carries their phase bits from call
+// to call) filled by the tensor unit through tmap (the state read, viewed as a 3D
 // array of 4 nx x ny x nz values); the tile must lie inside the box, and halo
 // nodes outside it are read from global memory (periodic images) or are walls.
 template <int Q, int ST, int H, bool AMAX, bool TMA = false>
 __device__ __forceinline__ void tile_column(const StepArgs& a, const Scales& sc, int x0, int y0, int z0, int z1,
                                             unsigned char* smem_raw, float (&amax)[4],
-                                            const CUtensorMap* tmap = nullptr)
+                                            const CUtensorMap* tmap = nullptr, uint32_t* phase_io = nullptr)
 {
     constexpr int TX = 32;
     using S = Storage<ST>;
@@ -270,14 +300,9 @@ __device__ __forceinline__ void tile_column(const StepArgs& a, const Scales& sc,
     [[maybe_unused]] int hcA = 0, hrA = 0, hcB = 0, hrB = 0;
     [[maybe_unused]] bool hinA = false, hinB = false;
     if constexpr (TMA) {
-        const uint32_t sbase = smem_u32(smem_raw);
-        stages = smem_raw + (((sbase + (uint32_t)C::SMEM + 127u) & ~127u) - sbase);
-        mbar = reinterpret_cast<uint64_t*>(stages + SC::NSTAGE * SC::STAGE_BYTES);
-        if (tid == 0) {
-#pragma unroll
-            for (int st = 0; st < SC::NSTAGE; ++st) mbar_init(&mbar[st], 1);
-            mbar_init_fence();
-        }
+        stages = stage_base<Q, ST, H>(smem_raw);
+        mbar = stage_barriers<Q, ST, H>(smem_raw);
+        phase = *phase_io;
         auto inside = [&](int x, int y) { return x >= 0 && x < a.nx && y >= 0 && y < a.ny; };
         if (hrow) {
             hcA = tx + SC::XOFF; hrA = 0; hinA = inside(gx, y0 - 1);
@@ -286,7 +311,6 @@ __device__ __forceinline__ void tile_column(const StepArgs& a, const Scales& sc,
             hcA = hctx + SC::XOFF; hrA = hcty + 1; hinA = inside(x0 + hctx, y0 + hcty);
             hcB = hctx + SC::XOFF; hrB = hcty + H + 1; hinB = inside(x0 + hctx, y0 + hcty + H);
         }
-        __syncthreads();
     }
     // thread 0 starts the copy of plane p's box into its stage
     [[maybe_unused]] auto issue = [&](int p) {
@@ -333,13 +357,16 @@ __device__ __forceinline__ void tile_column(const StepArgs& a, const Scales& sc,
     }
 
     NodeAcc<L, NC> acc;  // plane p - 1, all but its c_z = -1 links
-    L up_v[Q], up_s[Q];  // c_z = +1 links gathered for plane p: value, source sigma
     L own_in[Q];         // own outgoing (., ., +1) of plane p - 1
     L sig;               // own sigma of plane p (1 = solid or outside)
+    L sig_prev;          // own sigma of plane p - 1
+    L hprev[3];          // halo node's c_z = +1 exports of plane p - 1
+    L hs_prev;           // halo node's sigma of plane p - 1
     L out[Q];            // own outgoing values of plane p
     bool fluidA = false, fluidB = false, fluidA_prev = false, fluidB_prev = false;
 #pragma unroll
-    for (int k = 0; k < Q; ++k) up_v[k] = up_s[k] = own_in[k] = L(E(0));
+    for (int k = 0; k < Q; ++k) own_in[k] = L(E(0));
+    sig_prev = hs_prev = hprev[0] = hprev[1] = hprev[2] = L(E(0));
     acc.clear();
 
     struct Slot {
@@ -381,7 +408,7 @@ __device__ __forceinline__ void tile_column(const StepArgs& a, const Scales& sc,
             static_for<0, NB>([&](auto bc) {
                 constexpr int b = decltype(bc)::value;
                 constexpr int dx = X::dx(b), dy = X::dy(b);
-                const L vm = out[kdir(dx, dy, -1)], v0 = out[kdir(dx, dy, 0)], vp = out[kdir(dx, dy, 1)];
+                const L vm = out[kdir(dx, dy, -1)], v0 = out[kdir(dx, dy, 0)], vp = own_in[kdir(dx, dy, 1)];
                 L01[b * NPP + my] = V4<E>{vm.v.x, vm.v.y, v0.v.x, v0.v.y};
                 L2[b * NPP + my] = V2<E>{vp.v.x, vp.v.y};
             });
@@ -390,7 +417,7 @@ __device__ __forceinline__ void tile_column(const StepArgs& a, const Scales& sc,
                 const L v = out[kdir(X::ddx(j), X::ddy(j), 0)];
                 DG[j * NPP + my] = V2<E>{v.v.x, v.v.y};
             });
-            SG[my] = V2<E>{sig.v.x, sig.v.y};
+            reinterpret_cast<V4<E>*>(SG)[my] = V4<E>{sig_prev.v.x, sig_prev.v.y, sig.v.x, sig.v.y};
             // interior rows H-1 and H also appear in pair rows -1 (lane B) and H (lane A)
             if (ty == H - 1) {
                 const int q = ppos(tx, -1, PW);
@@ -399,14 +426,15 @@ __device__ __forceinline__ void tile_column(const StepArgs& a, const Scales& sc,
                     if constexpr (X::dy(b) == 1) {
                         L01[b * NPP + q].y = out[kdir(X::dx(b), 1, -1)].v.x;
                         L01[b * NPP + q].w = out[kdir(X::dx(b), 1, 0)].v.x;
-                        L2[b * NPP + q].y = out[kdir(X::dx(b), 1, 1)].v.x;
+                        L2[b * NPP + q].y = own_in[kdir(X::dx(b), 1, 1)].v.x;
                     }
                 });
                 static_for<0, ND>([&](auto jc) {
                     constexpr int j = decltype(jc)::value;
                     if constexpr (X::ddy(j) == 1) DG[j * NPP + q].y = out[kdir(X::ddx(j), 1, 0)].v.x;
                 });
-                SG[q].y = sig.v.x;
+                SG[2 * q].y = sig_prev.v.x;
+                SG[2 * q + 1].y = sig.v.x;
             }
             if (ty == 0) {
                 const int q = ppos(tx, H, PW);
@@ -415,14 +443,15 @@ __device__ __forceinline__ void tile_column(const StepArgs& a, const Scales& sc,
                     if constexpr (X::dy(b) == -1) {
                         L01[b * NPP + q].x = out[kdir(X::dx(b), -1, -1)].v.y;
                         L01[b * NPP + q].z = out[kdir(X::dx(b), -1, 0)].v.y;
-                        L2[b * NPP + q].x = out[kdir(X::dx(b), -1, 1)].v.y;
+                        L2[b * NPP + q].x = own_in[kdir(X::dx(b), -1, 1)].v.y;
                     }
                 });
                 static_for<0, ND>([&](auto jc) {
                     constexpr int j = decltype(jc)::value;
                     if constexpr (X::ddy(j) == -1) DG[j * NPP + q].x = out[kdir(X::ddx(j), -1, 0)].v.y;
                 });
-                SG[q].x = sig.v.y;
+                SG[2 * q].x = sig_prev.v.y;
+                SG[2 * q + 1].x = sig.v.y;
             }
 
             // ---- halo exports ----------------------------------------------------
@@ -434,19 +463,21 @@ __device__ __forceinline__ void tile_column(const StepArgs& a, const Scales& sc,
                 const L pb = m.Px;
                 auto f = [&](L pv) { return feq_scaled(m.A, m.H, pv); };
                 const int qA = ppos(tx, -1, PW), qB = ppos(tx, H, PW);
-                auto put = [&](int bA, int bB, L vm, L v0, L vp) {
+                // c_z = +1 values go out one plane late (hprev), like the interior's
+                auto put = [&](int bA, int bB, L vm, L v0, L vp, L& prev) {
                     L01[bA * NPP + qA].x = vm.v.x;
                     L01[bA * NPP + qA].z = v0.v.x;
-                    L2[bA * NPP + qA].x = vp.v.x;
+                    L2[bA * NPP + qA].x = prev.v.x;
                     L01[bB * NPP + qB].y = vm.v.y;
                     L01[bB * NPP + qB].w = v0.v.y;
-                    L2[bB * NPP + qB].y = vp.v.y;
+                    L2[bB * NPP + qB].y = prev.v.y;
+                    prev = vp;
                 };
-                put(block_of(0, 1), block_of(0, -1), f(pa - m.Pz), f(pa), f(pa + m.Pz));
+                put(block_of(0, 1), block_of(0, -1), f(pa - m.Pz), f(pa), f(pa + m.Pz), hprev[0]);
                 const L pp = pa + pb, pm = pa - pb;
                 if constexpr (Q == 27) {
-                    put(block_of(1, 1), block_of(1, -1), f(pp - m.Pz), f(pp), f(pp + m.Pz));
-                    put(block_of(-1, 1), block_of(-1, -1), f(pm - m.Pz), f(pm), f(pm + m.Pz));
+                    put(block_of(1, 1), block_of(1, -1), f(pp - m.Pz), f(pp), f(pp + m.Pz), hprev[1]);
+                    put(block_of(-1, 1), block_of(-1, -1), f(pm - m.Pz), f(pm), f(pm + m.Pz), hprev[2]);
                 } else {
                     const L vpp = f(pp), vpm = f(pm);
                     DG[diag_of(1, 1) * NPP + qA].x = vpp.v.x;
@@ -454,8 +485,11 @@ __device__ __forceinline__ void tile_column(const StepArgs& a, const Scales& sc,
                     DG[diag_of(-1, 1) * NPP + qA].x = vpm.v.x;
                     DG[diag_of(-1, -1) * NPP + qB].y = vpm.v.y;
                 }
-                SG[qA].x = hs.v.x;
-                SG[qB].y = hs.v.y;
+                SG[2 * qA].x = hs_prev.v.x;
+                SG[2 * qA + 1].x = hs.v.x;
+                SG[2 * qB].y = hs_prev.v.y;
+                SG[2 * qB + 1].y = hs.v.y;
+                hs_prev = hs;
             } else if (hcol) {
                 // both lanes: directions with dx = hcs
                 L hs;
@@ -463,21 +497,23 @@ __device__ __forceinline__ void tile_column(const StepArgs& a, const Scales& sc,
                 const L pa = m.Px * L(E(hcs));
                 const L pb = m.Py;
                 auto f = [&](L pv) { return feq_scaled(m.A, m.H, pv); };
-                auto put = [&](int b, L vm, L v0, L vp) {
+                auto put = [&](int b, L vm, L v0, L vp, L& prev) {
                     L01[b * NPP + hc_pos] = V4<E>{vm.v.x, vm.v.y, v0.v.x, v0.v.y};
-                    L2[b * NPP + hc_pos] = V2<E>{vp.v.x, vp.v.y};
+                    L2[b * NPP + hc_pos] = V2<E>{prev.v.x, prev.v.y};
+                    prev = vp;
                 };
-                put(hc_b0, f(pa - m.Pz), f(pa), f(pa + m.Pz));
+                put(hc_b0, f(pa - m.Pz), f(pa), f(pa + m.Pz), hprev[0]);
                 const L pp = pa + pb, pm = pa - pb;
                 if constexpr (Q == 27) {
-                    put(hc_bp, f(pp - m.Pz), f(pp), f(pp + m.Pz));
-                    put(hc_bm, f(pm - m.Pz), f(pm), f(pm + m.Pz));
+                    put(hc_bp, f(pp - m.Pz), f(pp), f(pp + m.Pz), hprev[1]);
+                    put(hc_bm, f(pm - m.Pz), f(pm), f(pm + m.Pz), hprev[2]);
                 } else {
                     const L vpp = f(pp), vpm = f(pm);
                     DG[hc_bp * NPP + hc_pos] = V2<E>{vpp.v.x, vpp.v.y};
                     DG[hc_bm * NPP + hc_pos] = V2<E>{vpm.v.x, vpm.v.y};
                 }
-                SG[hc_pos] = V2<E>{hs.v.x, hs.v.y};
+                reinterpret_cast<V4<E>*>(SG)[hc_pos] = V4<E>{hs_prev.v.x, hs_prev.v.y, hs.v.x, hs.v.y};
+                hs_prev = hs;
             }
         if constexpr (TMA) {
             if (p + 2 <= z1) issue(p + 2);
@@ -486,44 +522,36 @@ __device__ __forceinline__ void tile_column(const StepArgs& a, const Scales& sc,
         }
     };
 
-    // The c_z = +1 values of plane p (read after its barrier) wait in registers
-    // for plane p + 1; so do the own outgoing (., ., +1) values for its bounce-back.
-    auto carry = [&](const Slot& sl, const V2<E> (&fsg)[NB]) {
-        static_for<0, NB>([&](auto bc) {
-            constexpr int b = decltype(bc)::value;
-            constexpr int dx = X::dx(b), dy = X::dy(b), K = kdir(dx, dy, 1);
-            const V2<E> v = sl.L2[b * NPP + ppos(tx - dx, ty - dy, PW)];
-            up_v[K] = L(v.x, v.y);
-            up_s[K] = L(fsg[b].x, fsg[b].y);
-        });
-        up_v[KZP] = out[KZP];
-        up_s[KZP] = sig;
+    // The own outgoing (., ., +1) values and sigma of plane p are kept one plane:
+    // bounce-back of plane p's c_z = -1 links, and plane p + 1's exports.
+    auto carry = [&]() {
         static_for<1, Q>([&](auto kc) {
             constexpr int K = decltype(kc)::value;
             if constexpr (cvel(K, 2) == 1) own_in[K] = out[K];
         });
+        sig_prev = sig;
     };
 
     // Each in-plane source position of this thread, read once per plane:
-    // {c_z = -1, c_z = 0} values and sigma.
-    auto load_faces = [&](const Slot& sl, V4<E> (&f01)[NB], V2<E> (&fsg)[NB]) {
+    // {c_z = -1, c_z = 0} values and {sigma of plane p - 1, of plane p}.
+    auto load_faces = [&](const Slot& sl, V4<E> (&f01)[NB], V4<E> (&fsg)[NB]) {
         static_for<0, NB>([&](auto bc) {
             constexpr int b = decltype(bc)::value;
             const int q = ppos(tx - X::dx(b), ty - X::dy(b), PW);
             f01[b] = sl.L01[b * NPP + q];
-            fsg[b] = sl.SG[q];
+            fsg[b] = reinterpret_cast<const V4<E>*>(sl.SG)[q];
         });
     };
 
     // c_z = -1 values of plane p complete plane p - 1, which is stored if it is
     // this block's and fluid.
-    auto finish_prev = [&](int p, const V4<E> (&f01)[NB], const V2<E> (&fsg)[NB]) {
+    auto finish_prev = [&](int p, const V4<E> (&f01)[NB], const V4<E> (&fsg)[NB]) {
         L dn_v[Q], dn_s[Q];
         static_for<0, NB>([&](auto bc) {
             constexpr int b = decltype(bc)::value;
             constexpr int K = kdir(X::dx(b), X::dy(b), -1);
             dn_v[K] = L(f01[b].x, f01[b].y);
-            dn_s[K] = L(fsg[b].x, fsg[b].y);
+            dn_s[K] = L(fsg[b].z, fsg[b].w);
         });
         dn_v[KZM] = out[KZM];  // (0,0,-1): from the own node at plane p
         dn_s[KZM] = sig;
@@ -547,9 +575,19 @@ __device__ __forceinline__ void tile_column(const StepArgs& a, const Scales& sc,
         }
     };
 
-    // plane p: the c_z = +1 links gathered last arrival, then c_z = 0
-    auto start_plane = [&](const Slot& sl, const V4<E> (&f01)[NB], const V2<E> (&fsg)[NB]) {
+    // plane p: its c_z = +1 links (plane p - 1 values, exported late), then c_z = 0
+    auto start_plane = [&](const Slot& sl, const V4<E> (&f01)[NB], const V4<E> (&fsg)[NB]) {
         acc.S[0] = out[0];
+        L up_v[Q], up_s[Q];
+        static_for<0, NB>([&](auto bc) {
+            constexpr int b = decltype(bc)::value;
+            constexpr int dx = X::dx(b), dy = X::dy(b), K = kdir(dx, dy, 1);
+            const V2<E> v = sl.L2[b * NPP + ppos(tx - dx, ty - dy, PW)];
+            up_v[K] = L(v.x, v.y);
+            up_s[K] = L(fsg[b].x, fsg[b].y);
+        });
+        up_v[KZP] = own_in[KZP];  // (0,0,+1): from the own node at plane p - 1
+        up_s[KZP] = sig_prev;
         static_for<1, Q>([&](auto kc) {
             constexpr int K = decltype(kc)::value;
             if constexpr (cvel(K, 2) == 1) acc.template add<Q, K>(fma(up_s[K], out[inv_dir(K)], up_v[K]));
@@ -559,14 +597,14 @@ __device__ __forceinline__ void tile_column(const StepArgs& a, const Scales& sc,
             constexpr int b = decltype(bc)::value;
             constexpr int K = kdir(X::dx(b), X::dy(b), 0);
             mid_v[K] = L(f01[b].z, f01[b].w);
-            mid_s[K] = L(fsg[b].x, fsg[b].y);
+            mid_s[K] = L(fsg[b].z, fsg[b].w);
         });
         static_for<0, ND>([&](auto jc) {
             constexpr int j = decltype(jc)::value;
             constexpr int dx = X::ddx(j), dy = X::ddy(j), K = kdir(dx, dy, 0);
             const int q = ppos(tx - dx, ty - dy, PW);
             const V2<E> v = sl.DG[j * NPP + q];
-            const V2<E> s = sl.SG[q];
+            const V2<E> s = sl.SG[2 * q + 1];
             mid_v[K] = L(v.x, v.y);
             mid_s[K] = L(s.x, s.y);
         });
@@ -576,16 +614,9 @@ __device__ __forceinline__ void tile_column(const StepArgs& a, const Scales& sc,
         });
     };
 
-    // plane z0 - 1 (below the chunk): exports and carry only
+    // plane z0 - 1 (below the chunk): exports only
     export_plane(z0 - 1, true);
-    __syncthreads();
-    {
-        const Slot sl = slot_of(z0 - 1);
-        V4<E> f01[NB];
-        V2<E> fsg[NB];
-        load_faces(sl, f01, fsg);
-        carry(sl, fsg);
-    }
+    carry();
     // planes of the chunk; the first finish_prev completes plane z0 - 1,
     // which is not this block's (fluid*_prev are false) and is not stored
     for (int p = z0; p < z1; ++p) {
@@ -593,11 +624,11 @@ __device__ __forceinline__ void tile_column(const StepArgs& a, const Scales& sc,
         __syncthreads();
         const Slot sl = slot_of(p);
         V4<E> f01[NB];
-        V2<E> fsg[NB];
+        V4<E> fsg[NB];
         load_faces(sl, f01, fsg);
         finish_prev(p, f01, fsg);
         start_plane(sl, f01, fsg);
-        carry(sl, fsg);
+        carry();
         fluidA_prev = fluidA;
         fluidB_prev = fluidB;
     }
@@ -607,12 +638,13 @@ __device__ __forceinline__ void tile_column(const StepArgs& a, const Scales& sc,
     {
         const Slot sl = slot_of(z1);
         V4<E> f01[NB];
-        V2<E> fsg[NB];
+        V4<E> fsg[NB];
         load_faces(sl, f01, fsg);
         finish_prev(z1, f01, fsg);
     }
     if constexpr (TMA) {
         if (timed_out) atomicAdd(&g_tma_timeouts, 1u);
+        *phase_io = phase;
     }
 }
 
