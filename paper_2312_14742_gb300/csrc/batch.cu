@@ -10,10 +10,11 @@
 // arguments, read from the device table. Everything that changes from step to
 // step lives in the table on the device: which copy holds a box's current
 // state, its step count (the stochastic-rounding seed), its 16-bit scales.
-// Boxes whose tiles are all full are stepped by the staged (TMA) tile column
-// through their own tensor maps (one per state copy, in device memory); the
-// stage mbarriers are set up once per launch and their phases run on from
-// item to item. A launch therefore has the same arguments every step, and K steps can be
+// Boxes whose tiles are all full are stepped by a staged (TMA) instance of
+// the kernel through their own tensor maps (one per state copy, in device
+// memory; the stage mbarriers are set up once per launch and their phases run
+// on from item to item), the others by a register instance: two work tables,
+// one launch each per step. A launch therefore has the same arguments every step, and K steps can be
 // captured once in a CUDA graph and replayed while boxes come and go (the
 // host edits the table between replays).
 //
@@ -55,11 +56,12 @@ __device__ void finish_box(BatchDomain& R, int storage)
     const uint32_t c = R.cur;
     const int64_t step = R.step + 1;
     if (storage == ST_F16S || storage == ST_BF16S) {
-        float m[4];
-#pragma unroll
-        for (int f = 0; f < 4; ++f) m[f] = __uint_as_float(atomicExch(&R.amax[f], 0u));
         // buf[c ^ 1] was just written with scale[c ^ 1]; the next step writes buf[c]
         const bool check = storage == ST_F16S && step % BATCH_RESCALE_EVERY == 0;
+        float m[4] = {0.f, 0.f, 0.f, 0.f};
+        if (check)
+#pragma unroll
+            for (int f = 0; f < 4; ++f) m[f] = __uint_as_float(atomicExch(&R.amax[f], 0u));
 #pragma unroll
         for (int f = 0; f < 4; ++f) {
             const float s = check ? decide_scale(m, f, R.scale[c ^ 1][f], R.gfloor) : R.scale[c ^ 1][f];
@@ -71,15 +73,17 @@ __device__ void finish_box(BatchDomain& R, int storage)
     R.step = step;
 }
 
-template <int Q, int ST, int H, int MINB>
+template <int Q, int ST, int H, int MINB, bool TMA>
 __global__ void __launch_bounds__(32 * H, MINB) tau1_batch_kernel(BatchTable* T)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ int last;
-    constexpr bool AMAX = ST == ST_F16S || ST == ST_BF16S;
+    // FP16 only (BF16 keeps S = 1): maxima of the stored values, needed on the
+    // step before each scale check
+    constexpr bool AMAX = ST == ST_F16S;
     const int nitems = T->nitems, ndom = T->ndom, chunk = T->chunk;
     const int* __restrict__ begin = T->item_begin;
-    stage_init<Q, ST, H>(smem_raw);  // visible after the first item's barrier
+    if constexpr (TMA) stage_init<Q, ST, H>(smem_raw);  // visible after the first item's barrier
     uint32_t phase = 0;
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         // box of this item: the last d with begin[d] <= it
@@ -104,11 +108,11 @@ __global__ void __launch_bounds__(32 * H, MINB) tau1_batch_kernel(BatchTable* T)
         const int x0 = (tile % R.ntx) * 32, y0 = (tile / R.ntx) * (2 * H);
         float amax[4] = {0.f, 0.f, 0.f, 0.f};
         __syncthreads();  // the previous item's last shared-memory reads are done
-        if (R.tma)
+        if constexpr (TMA)
             tile_column<Q, ST, H, AMAX, true>(a, sc, x0, y0, z0, z1, smem_raw, amax, T->maps + 2 * slot + c, &phase);
         else
             tile_column<Q, ST, H, AMAX, false>(a, sc, x0, y0, z0, z1, smem_raw, amax);
-        if constexpr (AMAX) {
+        if (AMAX && (R.step + 1) % BATCH_RESCALE_EVERY == 0) {
 #pragma unroll
             for (int f = 0; f < 4; ++f) {
                 float m = amax[f];
@@ -131,13 +135,13 @@ __global__ void __launch_bounds__(32 * H, MINB) tau1_batch_kernel(BatchTable* T)
     if (threadIdx.x == 0) T->done = 0;
 }
 
-template <int Q, int ST, int V>
+template <int Q, int ST, int V, bool TMA>
 struct BatchKernel {
     using E = typename Storage<ST>::ctype;
     static constexpr int H = Shape<Q, E, V>::H;
     using C = TCfg<Q, 32, H, E>;
-    static constexpr size_t SMEM = tile_smem<Q, ST, H, true>();
-    static constexpr auto fn() { return tau1_batch_kernel<Q, ST, H, Shape<Q, E, V>::MINB>; }
+    static constexpr size_t SMEM = tile_smem<Q, ST, H, TMA>();
+    static constexpr auto fn() { return tau1_batch_kernel<Q, ST, H, Shape<Q, E, V>::MINB, TMA>; }
     static cudaError_t prepare(int& grid, int& tile_h)
     {
         auto kern = fn();
@@ -159,7 +163,7 @@ struct BatchKernel {
     }
 };
 
-template <int Q, int ST>
+template <int Q, int ST, bool TMA>
 cudaError_t dispatch_v(int variant, bool prep, BatchTable* T, int& grid, int& tile_h, cudaStream_t s)
 {
     auto go = [&](auto k) {
@@ -167,49 +171,52 @@ cudaError_t dispatch_v(int variant, bool prep, BatchTable* T, int& grid, int& ti
         return prep ? K::prepare(grid, tile_h) : K::launch(T, grid, s);
     };
     if constexpr (ST == ST_F64) {
-        return variant == 0 ? go(BatchKernel<Q, ST, 0>{}) : cudaErrorInvalidValue;
+        return variant == 0 ? go(BatchKernel<Q, ST, 0, TMA>{}) : cudaErrorInvalidValue;
     } else {
         switch (variant) {
-        case 0: return go(BatchKernel<Q, ST, 0>{});
-        case 1: return go(BatchKernel<Q, ST, 1>{});
-        case 2: return go(BatchKernel<Q, ST, 2>{});
-        case 3: return go(BatchKernel<Q, ST, 3>{});
+        case 0: return go(BatchKernel<Q, ST, 0, TMA>{});
+        case 1: return go(BatchKernel<Q, ST, 1, TMA>{});
+        case 2: return go(BatchKernel<Q, ST, 2, TMA>{});
+        case 3: return go(BatchKernel<Q, ST, 3, TMA>{});
         default: return cudaErrorInvalidValue;
         }
     }
 }
 
+template <bool TMA>
 cudaError_t dispatch(int q, int storage, int variant, bool prep, BatchTable* T, int& grid, int& tile_h,
                      cudaStream_t s)
 {
     switch (q * 10 + storage) {
-    case 190 + ST_F64: return dispatch_v<19, ST_F64>(variant, prep, T, grid, tile_h, s);
-    case 190 + ST_F32: return dispatch_v<19, ST_F32>(variant, prep, T, grid, tile_h, s);
-    case 190 + ST_F16S: return dispatch_v<19, ST_F16S>(variant, prep, T, grid, tile_h, s);
-    case 190 + ST_BF16S: return dispatch_v<19, ST_BF16S>(variant, prep, T, grid, tile_h, s);
-    case 270 + ST_F64: return dispatch_v<27, ST_F64>(variant, prep, T, grid, tile_h, s);
-    case 270 + ST_F32: return dispatch_v<27, ST_F32>(variant, prep, T, grid, tile_h, s);
-    case 270 + ST_F16S: return dispatch_v<27, ST_F16S>(variant, prep, T, grid, tile_h, s);
-    case 270 + ST_BF16S: return dispatch_v<27, ST_BF16S>(variant, prep, T, grid, tile_h, s);
+    case 190 + ST_F64: return dispatch_v<19, ST_F64, TMA>(variant, prep, T, grid, tile_h, s);
+    case 190 + ST_F32: return dispatch_v<19, ST_F32, TMA>(variant, prep, T, grid, tile_h, s);
+    case 190 + ST_F16S: return dispatch_v<19, ST_F16S, TMA>(variant, prep, T, grid, tile_h, s);
+    case 190 + ST_BF16S: return dispatch_v<19, ST_BF16S, TMA>(variant, prep, T, grid, tile_h, s);
+    case 270 + ST_F64: return dispatch_v<27, ST_F64, TMA>(variant, prep, T, grid, tile_h, s);
+    case 270 + ST_F32: return dispatch_v<27, ST_F32, TMA>(variant, prep, T, grid, tile_h, s);
+    case 270 + ST_F16S: return dispatch_v<27, ST_F16S, TMA>(variant, prep, T, grid, tile_h, s);
+    case 270 + ST_BF16S: return dispatch_v<27, ST_BF16S, TMA>(variant, prep, T, grid, tile_h, s);
     default: return cudaErrorInvalidValue;
     }
 }
 
 }  // namespace
 
-cudaError_t batch_prepare(int q, int storage, int variant, int* grid, int* tile_h)
+cudaError_t batch_prepare(int q, int storage, int variant, bool tma, int* grid, int* tile_h)
 {
     int g = 0, th = 0;
-    cudaError_t e = dispatch(q, storage, variant, true, nullptr, g, th, nullptr);
+    cudaError_t e = tma ? dispatch<true>(q, storage, variant, true, nullptr, g, th, nullptr)
+                        : dispatch<false>(q, storage, variant, true, nullptr, g, th, nullptr);
     *grid = g;
     *tile_h = th;
     return e;
 }
 
-cudaError_t launch_tau1_batch(int q, int storage, int variant, BatchTable* T, int grid, cudaStream_t s)
+cudaError_t launch_tau1_batch(int q, int storage, int variant, bool tma, BatchTable* T, int grid, cudaStream_t s)
 {
     int th = 0;
-    return dispatch(q, storage, variant, false, T, grid, th, s);
+    return tma ? dispatch<true>(q, storage, variant, false, T, grid, th, s)
+               : dispatch<false>(q, storage, variant, false, T, grid, th, s);
 }
 
 }  // namespace lbm

@@ -34,8 +34,9 @@ struct BatchTable {
     const CUtensorMap* maps; // [capacity][2] tensor maps of buf[0], buf[1] (boxes with tma)
 };
 
-// Persistent grid size and tile height (2H) of a kernel variant.
-cudaError_t batch_prepare(int q, int storage, int variant, int* grid, int* tile_h);
-cudaError_t launch_tau1_batch(int q, int storage, int variant, BatchTable* T, int grid, cudaStream_t s);
+// Persistent grid size and tile height (2H) of a kernel variant, in its
+// staged (tma) or register instance.
+cudaError_t batch_prepare(int q, int storage, int variant, bool tma, int* grid, int* tile_h);
+cudaError_t launch_tau1_batch(int q, int storage, int variant, bool tma, BatchTable* T, int grid, cudaStream_t s);
 
 }  // namespace lbm

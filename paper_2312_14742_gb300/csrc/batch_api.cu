@@ -38,6 +38,7 @@ struct Slot {
     uint64_t bytes = 0;
     int64_t steps = 0;
     int ntiles = 0;  // tiles per plane
+    int tma = 0;     // stepped by the staged instance (table 1), else table 0
 };
 
 uint64_t round256(uint64_t b) { return (b + 255) & ~(uint64_t)255; }
@@ -51,14 +52,17 @@ struct lbm_tau1_batch {
     cudaStream_t capture = nullptr;  // private stream for graph capture
     cudaEvent_t side_done = nullptr;
     std::vector<Slot> slots;
-    BatchTable* dtable = nullptr;
+    // two work tables: [0] boxes stepped by the register instance, [1] by the
+    // staged (TMA) instance; both index the same box records
+    BatchTable* dtable[2] = {};
     BatchDomain* ddom = nullptr;
-    int* dlive = nullptr;
-    int* dbegin = nullptr;
+    int* dlive[2] = {};
+    int* dbegin[2] = {};
+    bool nonempty[2] = {};
     CUtensorMap* dmaps = nullptr;  // [capacity][2]
     Stage ring[RING];
     int ring_pos = 0;
-    int grid = 0, tile_h = 0;
+    int grid[2] = {}, tile_h = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     uint64_t budget = 0, used = 0;
@@ -123,61 +127,91 @@ cudaError_t stage_done(Stage* s, cudaStream_t stream)
 // Work items of a box for a chunk height.
 int box_items(const Slot& s, int chunk) { return s.ntiles * ((s.cfg.nz + chunk - 1) / chunk); }
 
-// Rebuilds the live list and item offsets and queues their upload. The chunk
-// is the tallest of 32, 16, 8 planes that still gives at least two items per
-// block of the persistent grid, else 4.
+// Rebuilds the live lists and item offsets of both tables and queues their
+// upload. A table's chunk is the tallest of 32, 16, 8 planes that still gives
+// at least two items per block of its persistent grid, else 4. A change in
+// which tables are empty drops the captured graph (it launches only the
+// non-empty ones).
 lbm_status upload_table(lbm_tau1_batch* b)
 {
-    int chunk = 32;
-    for (; chunk > 4; chunk /= 2) {
-        int64_t tot = 0;
-        for (const Slot& s : b->slots)
-            if (s.live) tot += box_items(s, chunk);
-        if (tot >= 2 * (int64_t)b->grid) break;
-    }
-    std::vector<int> live, begin;
-    int items = 0;
-    for (int i = 0; i < (int)b->slots.size(); ++i)
-        if (b->slots[i].live) {
-            live.push_back(i);
-            begin.push_back(items);
-            items += box_items(b->slots[i], chunk);
+    int nlive = 0;
+    for (int t = 0; t < 2; ++t) {
+        int chunk = 32;
+        for (; chunk > 4; chunk /= 2) {
+            int64_t tot = 0;
+            for (const Slot& s : b->slots)
+                if (s.live && s.tma == t) tot += box_items(s, chunk);
+            if (tot >= 2 * (int64_t)b->grid[t]) break;
         }
-    const int nd = (int)live.size();
-    BatchTable hdr{};
-    hdr.nitems = items;
-    hdr.ndom = nd;
-    hdr.done = 0;
-    hdr.chunk = chunk;
-    hdr.live = b->dlive;
-    hdr.item_begin = b->dbegin;
-    hdr.dom = b->ddom;
-    hdr.maps = b->dmaps;
-    const size_t lb = (size_t)nd * sizeof(int);
-    Stage* s = nullptr;
-    BCUDA(b, stage_get(b, sizeof(hdr) + 2 * lb + 16, &s), "batch: staging buffer");
-    unsigned char* p = static_cast<unsigned char*>(s->p);
-    std::memcpy(p, &hdr, sizeof(hdr));
-    if (nd) {
-        std::memcpy(p + sizeof(hdr), live.data(), lb);
-        std::memcpy(p + sizeof(hdr) + lb, begin.data(), lb);
-        BCUDA(b, cudaMemcpyAsync(b->dlive, p + sizeof(hdr), lb, cudaMemcpyHostToDevice, b->stream), "batch: table copy");
-        BCUDA(b, cudaMemcpyAsync(b->dbegin, p + sizeof(hdr) + lb, lb, cudaMemcpyHostToDevice, b->stream),
+        std::vector<int> live, begin;
+        int items = 0;
+        for (int i = 0; i < (int)b->slots.size(); ++i)
+            if (b->slots[i].live && b->slots[i].tma == t) {
+                live.push_back(i);
+                begin.push_back(items);
+                items += box_items(b->slots[i], chunk);
+            }
+        const int nd = (int)live.size();
+        BatchTable hdr{};
+        hdr.nitems = items;
+        hdr.ndom = nd;
+        hdr.done = 0;
+        hdr.chunk = chunk;
+        hdr.live = b->dlive[t];
+        hdr.item_begin = b->dbegin[t];
+        hdr.dom = b->ddom;
+        hdr.maps = b->dmaps;
+        const size_t lb = (size_t)nd * sizeof(int);
+        Stage* st = nullptr;
+        BCUDA(b, stage_get(b, sizeof(hdr) + 2 * lb + 16, &st), "batch: staging buffer");
+        unsigned char* p = static_cast<unsigned char*>(st->p);
+        std::memcpy(p, &hdr, sizeof(hdr));
+        if (nd) {
+            std::memcpy(p + sizeof(hdr), live.data(), lb);
+            std::memcpy(p + sizeof(hdr) + lb, begin.data(), lb);
+            BCUDA(b, cudaMemcpyAsync(b->dlive[t], p + sizeof(hdr), lb, cudaMemcpyHostToDevice, b->stream),
+                  "batch: table copy");
+            BCUDA(b, cudaMemcpyAsync(b->dbegin[t], p + sizeof(hdr) + lb, lb, cudaMemcpyHostToDevice, b->stream),
+                  "batch: table copy");
+        }
+        BCUDA(b, cudaMemcpyAsync(b->dtable[t], p, sizeof(hdr), cudaMemcpyHostToDevice, b->stream),
               "batch: table copy");
+        BCUDA(b, stage_done(st, b->stream), "batch: staging event");
+        if ((nd > 0) != b->nonempty[t] && b->gexec) {
+            // the graph's launches follow which tables are non-empty
+            BCUDA(b, cudaStreamSynchronize(b->stream), "batch: sync before graph rebuild");
+            cudaGraphExecDestroy(b->gexec);
+            cudaGraphDestroy(b->graph);
+            b->gexec = nullptr;
+            b->graph = nullptr;
+        }
+        b->nonempty[t] = nd > 0;
+        nlive += nd;
     }
-    BCUDA(b, cudaMemcpyAsync(b->dtable, p, sizeof(hdr), cudaMemcpyHostToDevice, b->stream), "batch: table copy");
-    BCUDA(b, stage_done(s, b->stream), "batch: staging event");
-    b->nlive = nd;
+    b->nlive = nlive;
     return LBM_OK;
 }
+
+// One step of every live box: one launch per non-empty table.
+cudaError_t launch_step_tables(lbm_tau1_batch* b, cudaStream_t s)
+{
+    for (int t = 1; t >= 0; --t)
+        if (b->nonempty[t]) {
+            cudaError_t e = launch_tau1_batch(b->cfg.q, b->cfg.storage, b->cfg.variant, t == 1, b->dtable[t],
+                                              b->grid[t], s);
+            if (e != cudaSuccess) return e;
+        }
+    return cudaSuccess;
+}
+
+int launches_per_step(const lbm_tau1_batch* b) { return (b->nonempty[0] ? 1 : 0) + (b->nonempty[1] ? 1 : 0); }
 
 lbm_status capture_graph(lbm_tau1_batch* b)
 {
     const int k = b->cfg.graph_steps;
     BCUDA(b, cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal), "batch: begin capture");
     cudaError_t le = cudaSuccess;
-    for (int i = 0; i < k && le == cudaSuccess; ++i)
-        le = launch_tau1_batch(b->cfg.q, b->cfg.storage, b->cfg.variant, b->dtable, b->grid, b->capture);
+    for (int i = 0; i < k && le == cudaSuccess; ++i) le = launch_step_tables(b, b->capture);
     cudaGraph_t g = nullptr;
     cudaError_t ee = cudaStreamEndCapture(b->capture, &g);
     if (le != cudaSuccess || ee != cudaSuccess) {
@@ -212,10 +246,12 @@ void free_batch(lbm_tau1_batch* b)
         if (s.ev) { cudaEventSynchronize(s.ev); cudaEventDestroy(s.ev); }
         if (s.p) cudaFreeHost(s.p);
     }
-    if (b->dtable) cudaFree(b->dtable);
+    for (int t = 0; t < 2; ++t) {
+        if (b->dtable[t]) cudaFree(b->dtable[t]);
+        if (b->dlive[t]) cudaFree(b->dlive[t]);
+        if (b->dbegin[t]) cudaFree(b->dbegin[t]);
+    }
     if (b->ddom) cudaFree(b->ddom);
-    if (b->dlive) cudaFree(b->dlive);
-    if (b->dbegin) cudaFree(b->dbegin);
     if (b->dmaps) cudaFree(b->dmaps);
     if (b->red_partials) cudaFree(b->red_partials);
     if (b->red_out) cudaFree(b->red_out);
@@ -272,14 +308,17 @@ lbm_status lbm_tau1_batch_create(const lbm_tau1_batch_config* cfg, lbm_tau1_batc
     b->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
     b->slots.resize((size_t)cfg->capacity);
     const int cap = cfg->capacity;
-    cudaError_t e = batch_prepare(cfg->q, cfg->storage, cfg->variant, &b->grid, &b->tile_h);
+    cudaError_t e = batch_prepare(cfg->q, cfg->storage, cfg->variant, false, &b->grid[0], &b->tile_h);
+    if (e == cudaSuccess) e = batch_prepare(cfg->q, cfg->storage, cfg->variant, true, &b->grid[1], &b->tile_h);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->side_done, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaMalloc(&b->dtable, sizeof(BatchTable));
+    for (int t = 0; t < 2; ++t) {
+        if (e == cudaSuccess) e = cudaMalloc(&b->dtable[t], sizeof(BatchTable));
+        if (e == cudaSuccess) e = cudaMalloc(&b->dlive[t], (size_t)cap * sizeof(int));
+        if (e == cudaSuccess) e = cudaMalloc(&b->dbegin[t], (size_t)cap * sizeof(int));
+    }
     if (e == cudaSuccess) e = cudaMalloc(&b->ddom, (size_t)cap * sizeof(BatchDomain));
-    if (e == cudaSuccess) e = cudaMalloc(&b->dlive, (size_t)cap * sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc(&b->dbegin, (size_t)cap * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&b->dmaps, (size_t)cap * 2 * sizeof(CUtensorMap));
     if (e == cudaSuccess) e = cudaMalloc(&b->red_partials, (size_t)1024 * RED_FIELDS * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&b->red_out, (size_t)cap * RED_FIELDS * sizeof(double));
@@ -415,6 +454,7 @@ lbm_status lbm_tau1_batch_admit(lbm_tau1_batch* b, const lbm_tau1_config* cfg, c
     s.bytes = need;
     s.steps = 0;
     s.ntiles = rec.ntiles;
+    s.tma = rec.tma;
     b->used += need;
     if (lbm_status r = upload_table(b)) return r;
     *slot = id;
@@ -451,12 +491,11 @@ lbm_status lbm_tau1_batch_step(lbm_tau1_batch* b, int64_t nsteps)
         if (lbm_status st = capture_graph(b)) return st;
     for (; left >= k; left -= k) {
         BCUDA(b, cudaGraphLaunch(b->gexec, b->stream), "batch_step: graph launch");
-        b->launches += k;
+        b->launches += k * launches_per_step(b);
     }
     for (; left > 0; --left) {
-        BCUDA(b, launch_tau1_batch(b->cfg.q, b->cfg.storage, b->cfg.variant, b->dtable, b->grid, b->stream),
-              "batch_step: launch");
-        ++b->launches;
+        BCUDA(b, launch_step_tables(b, b->stream), "batch_step: launch");
+        b->launches += launches_per_step(b);
     }
     for (Slot& s : b->slots)
         if (s.live) s.steps += nsteps;

@@ -24,15 +24,12 @@
 // rows -1 and H. Halo nodes export only the directions pointing into the tile.
 //
 // At the "arrival" of plane p every position stores, per in-plane direction
-// (dx, dy) != 0, its values for c_z = -1 and 0 of plane p, its c_z = +1 value
-// of plane p - 1, and its solid fraction sigma of planes p - 1 and p (1 for a
-// solid node or a position beyond a non-periodic face, else 0). Solid nodes
-// export 0. After one barrier each thread gathers: c_z = -1 values complete
-// destination plane p - 1; the c_z = +1 values of plane p - 1 and the c_z = 0
-// values of plane p go into plane p; (0,0,+-1) and rest never leave the
-// thread. A node keeps its own c_z = +1 values one plane for its bounce-back
-// anyway, so exporting them one plane late costs no register, while the
-// receivers carry nothing across the plane loop. Walls (Algorithm "Complete Tau1 ... halfway
+// (dx, dy) != 0, its values for c_z = -1, 0, +1 and its solid fraction
+// sigma (1 for a solid node or a position beyond a non-periodic face, else
+// 0). Solid nodes export 0. After one barrier each thread gathers: c_z = -1
+// values complete destination plane p - 1, c_z = 0 values go into plane p,
+// c_z = +1 values wait one arrival in registers; (0,0,+-1) and rest never
+// leave the thread. Walls (Algorithm "Complete Tau1 ... halfway
 // bounce-back") enter every link as fma(sigma, b, v), where v is the
 // gathered value and b the destination node's own outgoing value in
 // direction inv(k): v for a fluid source, b for a wall, with no branch.
@@ -93,13 +90,12 @@ template <int Q, int TX, int H, typename E> struct TCfg {
     static constexpr int PW = TX + 2;
     static constexpr int NPP = (TX + 2) * (H + 2);  // pair positions
     static constexpr int NT = TX * H;
-    // slot of plane p: L01[NB][NPP] {c_z=-1: A, B; c_z=0: A, B} | L2[NB][NPP]
-    //       {c_z=+1 of plane p-1: A, B} | DG[ND][NPP] {A, B}
-    //       | SG[NPP][2] {sigma of plane p-1: A, B}, {sigma of plane p: A, B}
+    // slot: L01[NB][NPP] {c_z=-1: A, B; c_z=0: A, B} | L2[NB][NPP] {c_z=+1: A, B}
+    //       | DG[ND][NPP] {A, B} | SG[NPP] {sigma A, sigma B}
     static constexpr size_t L01_BYTES = (size_t)NB * NPP * sizeof(V4<E>);
     static constexpr size_t L2_BYTES = (size_t)NB * NPP * sizeof(V2<E>);
     static constexpr size_t DG_BYTES = (size_t)ND * NPP * sizeof(V2<E>);
-    static constexpr size_t SG_BYTES = (size_t)NPP * 2 * sizeof(V2<E>);
+    static constexpr size_t SG_BYTES = (size_t)NPP * sizeof(V2<E>);
     static constexpr size_t SLOT_BYTES = L01_BYTES + L2_BYTES + DG_BYTES + SG_BYTES;
     static constexpr size_t SMEM = 2 * SLOT_BYTES;
     static_assert(TX == 32, "a warp is one tile row");
@@ -357,16 +353,13 @@ __device__ __forceinline__ void tile_column(const StepArgs& a, const Scales& sc,
     }
 
     NodeAcc<L, NC> acc;  // plane p - 1, all but its c_z = -1 links
+    L up_v[Q], up_s[Q];  // c_z = +1 links gathered for plane p: value, source sigma
     L own_in[Q];         // own outgoing (., ., +1) of plane p - 1
     L sig;               // own sigma of plane p (1 = solid or outside)
-    L sig_prev;          // own sigma of plane p - 1
-    L hprev[3];          // halo node's c_z = +1 exports of plane p - 1
-    L hs_prev;           // halo node's sigma of plane p - 1
     L out[Q];            // own outgoing values of plane p
     bool fluidA = false, fluidB = false, fluidA_prev = false, fluidB_prev = false;
 #pragma unroll
-    for (int k = 0; k < Q; ++k) own_in[k] = L(E(0));
-    sig_prev = hs_prev = hprev[0] = hprev[1] = hprev[2] = L(E(0));
+    for (int k = 0; k < Q; ++k) up_v[k] = up_s[k] = own_in[k] = L(E(0));
     acc.clear();
 
     struct Slot {
@@ -408,7 +401,7 @@ __device__ __forceinline__ void tile_column(const StepArgs& a, const Scales& sc,
             static_for<0, NB>([&](auto bc) {
                 constexpr int b = decltype(bc)::value;
                 constexpr int dx = X::dx(b), dy = X::dy(b);
-                const L vm = out[kdir(dx, dy, -1)], v0 = out[kdir(dx, dy, 0)], vp = own_in[kdir(dx, dy, 1)];
+                const L vm = out[kdir(dx, dy, -1)], v0 = out[kdir(dx, dy, 0)], vp = out[kdir(dx, dy, 1)];
                 L01[b * NPP + my] = V4<E>{vm.v.x, vm.v.y, v0.v.x, v0.v.y};
                 L2[b * NPP + my] = V2<E>{vp.v.x, vp.v.y};
             });
@@ -417,7 +410,7 @@ __device__ __forceinline__ void tile_column(const StepArgs& a, const Scales& sc,
                 const L v = out[kdir(X::ddx(j), X::ddy(j), 0)];
                 DG[j * NPP + my] = V2<E>{v.v.x, v.v.y};
             });
-            reinterpret_cast<V4<E>*>(SG)[my] = V4<E>{sig_prev.v.x, sig_prev.v.y, sig.v.x, sig.v.y};
+            SG[my] = V2<E>{sig.v.x, sig.v.y};
             // interior rows H-1 and H also appear in pair rows -1 (lane B) and H (lane A)
             if (ty == H - 1) {
                 const int q = ppos(tx, -1, PW);
@@ -426,15 +419,14 @@ __device__ __forceinline__ void tile_column(const StepArgs& a, const Scales& sc,
                     if constexpr (X::dy(b) == 1) {
                         L01[b * NPP + q].y = out[kdir(X::dx(b), 1, -1)].v.x;
                         L01[b * NPP + q].w = out[kdir(X::dx(b), 1, 0)].v.x;
-                        L2[b * NPP + q].y = own_in[kdir(X::dx(b), 1, 1)].v.x;
+                        L2[b * NPP + q].y = out[kdir(X::dx(b), 1, 1)].v.x;
                     }
                 });
                 static_for<0, ND>([&](auto jc) {
                     constexpr int j = decltype(jc)::value;
                     if constexpr (X::ddy(j) == 1) DG[j * NPP + q].y = out[kdir(X::ddx(j), 1, 0)].v.x;
                 });
-                SG[2 * q].y = sig_prev.v.x;
-                SG[2 * q + 1].y = sig.v.x;
+                SG[q].y = sig.v.x;
             }
             if (ty == 0) {
                 const int q = ppos(tx, H, PW);
@@ -443,15 +435,14 @@ __device__ __forceinline__ void tile_column(const StepArgs& a, const Scales& sc,
                     if constexpr (X::dy(b) == -1) {
                         L01[b * NPP + q].x = out[kdir(X::dx(b), -1, -1)].v.y;
                         L01[b * NPP + q].z = out[kdir(X::dx(b), -1, 0)].v.y;
-                        L2[b * NPP + q].x = own_in[kdir(X::dx(b), -1, 1)].v.y;
+                        L2[b * NPP + q].x = out[kdir(X::dx(b), -1, 1)].v.y;
                     }
                 });
                 static_for<0, ND>([&](auto jc) {
                     constexpr int j = decltype(jc)::value;
                     if constexpr (X::ddy(j) == -1) DG[j * NPP + q].x = out[kdir(X::ddx(j), -1, 0)].v.y;
                 });
-                SG[2 * q].x = sig_prev.v.y;
-                SG[2 * q + 1].x = sig.v.y;
+                SG[q].x = sig.v.y;
             }
 
             // ---- halo exports ----------------------------------------------------
@@ -463,21 +454,19 @@ __device__ __forceinline__ void tile_column(const StepArgs& a, const Scales& sc,
                 const L pb = m.Px;
                 auto f = [&](L pv) { return feq_scaled(m.A, m.H, pv); };
                 const int qA = ppos(tx, -1, PW), qB = ppos(tx, H, PW);
-                // c_z = +1 values go out one plane late (hprev), like the interior's
-                auto put = [&](int bA, int bB, L vm, L v0, L vp, L& prev) {
+                auto put = [&](int bA, int bB, L vm, L v0, L vp) {
                     L01[bA * NPP + qA].x = vm.v.x;
                     L01[bA * NPP + qA].z = v0.v.x;
-                    L2[bA * NPP + qA].x = prev.v.x;
+                    L2[bA * NPP + qA].x = vp.v.x;
                     L01[bB * NPP + qB].y = vm.v.y;
                     L01[bB * NPP + qB].w = v0.v.y;
-                    L2[bB * NPP + qB].y = prev.v.y;
-                    prev = vp;
+                    L2[bB * NPP + qB].y = vp.v.y;
                 };
-                put(block_of(0, 1), block_of(0, -1), f(pa - m.Pz), f(pa), f(pa + m.Pz), hprev[0]);
+                put(block_of(0, 1), block_of(0, -1), f(pa - m.Pz), f(pa), f(pa + m.Pz));
                 const L pp = pa + pb, pm = pa - pb;
                 if constexpr (Q == 27) {
-                    put(block_of(1, 1), block_of(1, -1), f(pp - m.Pz), f(pp), f(pp + m.Pz), hprev[1]);
-                    put(block_of(-1, 1), block_of(-1, -1), f(pm - m.Pz), f(pm), f(pm + m.Pz), hprev[2]);
+                    put(block_of(1, 1), block_of(1, -1), f(pp - m.Pz), f(pp), f(pp + m.Pz));
+                    put(block_of(-1, 1), block_of(-1, -1), f(pm - m.Pz), f(pm), f(pm + m.Pz));
                 } else {
                     const L vpp = f(pp), vpm = f(pm);
                     DG[diag_of(1, 1) * NPP + qA].x = vpp.v.x;
@@ -485,11 +474,8 @@ __device__ __forceinline__ void tile_column(const StepArgs& a, const Scales& sc,
                     DG[diag_of(-1, 1) * NPP + qA].x = vpm.v.x;
                     DG[diag_of(-1, -1) * NPP + qB].y = vpm.v.y;
                 }
-                SG[2 * qA].x = hs_prev.v.x;
-                SG[2 * qA + 1].x = hs.v.x;
-                SG[2 * qB].y = hs_prev.v.y;
-                SG[2 * qB + 1].y = hs.v.y;
-                hs_prev = hs;
+                SG[qA].x = hs.v.x;
+                SG[qB].y = hs.v.y;
             } else if (hcol) {
                 // both lanes: directions with dx = hcs
                 L hs;
@@ -497,23 +483,21 @@ __device__ __forceinline__ void tile_column(const StepArgs& a, const Scales& sc,
                 const L pa = m.Px * L(E(hcs));
                 const L pb = m.Py;
                 auto f = [&](L pv) { return feq_scaled(m.A, m.H, pv); };
-                auto put = [&](int b, L vm, L v0, L vp, L& prev) {
+                auto put = [&](int b, L vm, L v0, L vp) {
                     L01[b * NPP + hc_pos] = V4<E>{vm.v.x, vm.v.y, v0.v.x, v0.v.y};
-                    L2[b * NPP + hc_pos] = V2<E>{prev.v.x, prev.v.y};
-                    prev = vp;
+                    L2[b * NPP + hc_pos] = V2<E>{vp.v.x, vp.v.y};
                 };
-                put(hc_b0, f(pa - m.Pz), f(pa), f(pa + m.Pz), hprev[0]);
+                put(hc_b0, f(pa - m.Pz), f(pa), f(pa + m.Pz));
                 const L pp = pa + pb, pm = pa - pb;
                 if constexpr (Q == 27) {
-                    put(hc_bp, f(pp - m.Pz), f(pp), f(pp + m.Pz), hprev[1]);
-                    put(hc_bm, f(pm - m.Pz), f(pm), f(pm + m.Pz), hprev[2]);
+                    put(hc_bp, f(pp - m.Pz), f(pp), f(pp + m.Pz));
+                    put(hc_bm, f(pm - m.Pz), f(pm), f(pm + m.Pz));
                 } else {
                     const L vpp = f(pp), vpm = f(pm);
                     DG[hc_bp * NPP + hc_pos] = V2<E>{vpp.v.x, vpp.v.y};
                     DG[hc_bm * NPP + hc_pos] = V2<E>{vpm.v.x, vpm.v.y};
                 }
-                reinterpret_cast<V4<E>*>(SG)[hc_pos] = V4<E>{hs_prev.v.x, hs_prev.v.y, hs.v.x, hs.v.y};
-                hs_prev = hs;
+                SG[hc_pos] = V2<E>{hs.v.x, hs.v.y};
             }
         if constexpr (TMA) {
             if (p + 2 <= z1) issue(p + 2);
@@ -522,36 +506,44 @@ __device__ __forceinline__ void tile_column(const StepArgs& a, const Scales& sc,
         }
     };
 
-    // The own outgoing (., ., +1) values and sigma of plane p are kept one plane:
-    // bounce-back of plane p's c_z = -1 links, and plane p + 1's exports.
-    auto carry = [&]() {
+    // The c_z = +1 values of plane p (read after its barrier) wait in registers
+    // for plane p + 1; so do the own outgoing (., ., +1) values for its bounce-back.
+    auto carry = [&](const Slot& sl, const V2<E> (&fsg)[NB]) {
+        static_for<0, NB>([&](auto bc) {
+            constexpr int b = decltype(bc)::value;
+            constexpr int dx = X::dx(b), dy = X::dy(b), K = kdir(dx, dy, 1);
+            const V2<E> v = sl.L2[b * NPP + ppos(tx - dx, ty - dy, PW)];
+            up_v[K] = L(v.x, v.y);
+            up_s[K] = L(fsg[b].x, fsg[b].y);
+        });
+        up_v[KZP] = out[KZP];
+        up_s[KZP] = sig;
         static_for<1, Q>([&](auto kc) {
             constexpr int K = decltype(kc)::value;
             if constexpr (cvel(K, 2) == 1) own_in[K] = out[K];
         });
-        sig_prev = sig;
     };
 
     // Each in-plane source position of this thread, read once per plane:
-    // {c_z = -1, c_z = 0} values and {sigma of plane p - 1, of plane p}.
-    auto load_faces = [&](const Slot& sl, V4<E> (&f01)[NB], V4<E> (&fsg)[NB]) {
+    // {c_z = -1, c_z = 0} values and sigma.
+    auto load_faces = [&](const Slot& sl, V4<E> (&f01)[NB], V2<E> (&fsg)[NB]) {
         static_for<0, NB>([&](auto bc) {
             constexpr int b = decltype(bc)::value;
             const int q = ppos(tx - X::dx(b), ty - X::dy(b), PW);
             f01[b] = sl.L01[b * NPP + q];
-            fsg[b] = reinterpret_cast<const V4<E>*>(sl.SG)[q];
+            fsg[b] = sl.SG[q];
         });
     };
 
     // c_z = -1 values of plane p complete plane p - 1, which is stored if it is
     // this block's and fluid.
-    auto finish_prev = [&](int p, const V4<E> (&f01)[NB], const V4<E> (&fsg)[NB]) {
+    auto finish_prev = [&](int p, const V4<E> (&f01)[NB], const V2<E> (&fsg)[NB]) {
         L dn_v[Q], dn_s[Q];
         static_for<0, NB>([&](auto bc) {
             constexpr int b = decltype(bc)::value;
             constexpr int K = kdir(X::dx(b), X::dy(b), -1);
             dn_v[K] = L(f01[b].x, f01[b].y);
-            dn_s[K] = L(fsg[b].z, fsg[b].w);
+            dn_s[K] = L(fsg[b].x, fsg[b].y);
         });
         dn_v[KZM] = out[KZM];  // (0,0,-1): from the own node at plane p
         dn_s[KZM] = sig;
@@ -575,19 +567,9 @@ __device__ __forceinline__ void tile_column(const StepArgs& a, const Scales& sc,
         }
     };
 
-    // plane p: its c_z = +1 links (plane p - 1 values, exported late), then c_z = 0
-    auto start_plane = [&](const Slot& sl, const V4<E> (&f01)[NB], const V4<E> (&fsg)[NB]) {
+    // plane p: the c_z = +1 links gathered last arrival, then c_z = 0
+    auto start_plane = [&](const Slot& sl, const V4<E> (&f01)[NB], const V2<E> (&fsg)[NB]) {
         acc.S[0] = out[0];
-        L up_v[Q], up_s[Q];
-        static_for<0, NB>([&](auto bc) {
-            constexpr int b = decltype(bc)::value;
-            constexpr int dx = X::dx(b), dy = X::dy(b), K = kdir(dx, dy, 1);
-            const V2<E> v = sl.L2[b * NPP + ppos(tx - dx, ty - dy, PW)];
-            up_v[K] = L(v.x, v.y);
-            up_s[K] = L(fsg[b].x, fsg[b].y);
-        });
-        up_v[KZP] = own_in[KZP];  // (0,0,+1): from the own node at plane p - 1
-        up_s[KZP] = sig_prev;
         static_for<1, Q>([&](auto kc) {
             constexpr int K = decltype(kc)::value;
             if constexpr (cvel(K, 2) == 1) acc.template add<Q, K>(fma(up_s[K], out[inv_dir(K)], up_v[K]));
@@ -597,14 +579,14 @@ __device__ __forceinline__ void tile_column(const StepArgs& a, const Scales& sc,
             constexpr int b = decltype(bc)::value;
             constexpr int K = kdir(X::dx(b), X::dy(b), 0);
             mid_v[K] = L(f01[b].z, f01[b].w);
-            mid_s[K] = L(fsg[b].z, fsg[b].w);
+            mid_s[K] = L(fsg[b].x, fsg[b].y);
         });
         static_for<0, ND>([&](auto jc) {
             constexpr int j = decltype(jc)::value;
             constexpr int dx = X::ddx(j), dy = X::ddy(j), K = kdir(dx, dy, 0);
             const int q = ppos(tx - dx, ty - dy, PW);
             const V2<E> v = sl.DG[j * NPP + q];
-            const V2<E> s = sl.SG[2 * q + 1];
+            const V2<E> s = sl.SG[q];
             mid_v[K] = L(v.x, v.y);
             mid_s[K] = L(s.x, s.y);
         });
@@ -614,9 +596,16 @@ __device__ __forceinline__ void tile_column(const StepArgs& a, const Scales& sc,
         });
     };
 
-    // plane z0 - 1 (below the chunk): exports only
+    // plane z0 - 1 (below the chunk): exports and carry only
     export_plane(z0 - 1, true);
-    carry();
+    __syncthreads();
+    {
+        const Slot sl = slot_of(z0 - 1);
+        V4<E> f01[NB];
+        V2<E> fsg[NB];
+        load_faces(sl, f01, fsg);
+        carry(sl, fsg);
+    }
     // planes of the chunk; the first finish_prev completes plane z0 - 1,
     // which is not this block's (fluid*_prev are false) and is not stored
     for (int p = z0; p < z1; ++p) {
@@ -624,11 +613,11 @@ __device__ __forceinline__ void tile_column(const StepArgs& a, const Scales& sc,
         __syncthreads();
         const Slot sl = slot_of(p);
         V4<E> f01[NB];
-        V4<E> fsg[NB];
+        V2<E> fsg[NB];
         load_faces(sl, f01, fsg);
         finish_prev(p, f01, fsg);
         start_plane(sl, f01, fsg);
-        carry();
+        carry(sl, fsg);
         fluidA_prev = fluidA;
         fluidB_prev = fluidB;
     }
@@ -638,7 +627,7 @@ __device__ __forceinline__ void tile_column(const StepArgs& a, const Scales& sc,
     {
         const Slot sl = slot_of(z1);
         V4<E> f01[NB];
-        V4<E> fsg[NB];
+        V2<E> fsg[NB];
         load_faces(sl, f01, fsg);
         finish_prev(z1, f01, fsg);
     }
