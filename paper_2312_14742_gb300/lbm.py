@@ -274,8 +274,10 @@ class Tau1:
     """One box: ``Tau1(q, (nx, ny, nz), storage="f32", periodic=(1,1,1), g=(gx,0,0))``."""
 
     def __init__(self, q: int, dims, storage: str = "f32", periodic=(1, 1, 1), g=(0.0, 0.0, 0.0),
-                 kernel: str = "auto", stream=None, scheme: int = LBM_SCHEME_TAU1, layout: int = LBM_DENSE):
+                 kernel: str = "auto", stream=None, scheme: int = LBM_SCHEME_TAU1, layout=LBM_DENSE):
         nx, ny, nz = (int(d) for d in dims)
+        if isinstance(layout, str):
+            layout = {"dense": LBM_DENSE, "sparse": LBM_SPARSE}[layout]
         cfg = lbm_tau1_config()
         cfg.q, cfg.storage, cfg.layout, cfg.scheme = int(q), STORAGE[storage], int(layout), int(scheme)
         cfg.nx, cfg.ny, cfg.nz = nx, ny, nz
