@@ -178,3 +178,26 @@ def test_fp16_batch_box_permeability_within_one_percent():
             B.step(50)
             ks.append(B.stats([s])[0]["permeability"])
     assert abs(np.mean(ks) - k64) <= 1e-2 * abs(k64), (np.mean(ks), k64)
+
+
+def test_batch_error_paths():
+    """Wrong lattice or storage, non-dense layout, a slot that is not live,
+    and a negative step count are refused without changing the batch."""
+    from paper_2312_14742_gb300 import lbm
+    solid = boxes(19)[0][0]
+    with Batch(19, "f32", capacity=4) as B:
+        s = B.admit(solid, (1, 1, 1), (1e-5, 0, 0))
+        for q, st, layout in ((27, "f32", lbm.LBM_DENSE), (19, "f64", lbm.LBM_DENSE), (19, "f32", lbm.LBM_SPARSE)):
+            cfg = lbm.box_config(q, solid.shape[::-1], st)
+            cfg.layout = layout
+            code, slot = lbm.lbm_tau1_batch_admit(B.b, cfg, solid.ctypes.data, 0)
+            assert code == lbm.LBM_EINVAL and slot == -1
+        assert lbm.lbm_tau1_batch_release(B.b, 3) == lbm.LBM_EINVAL
+        assert lbm.lbm_tau1_batch_release(B.b, -1) == lbm.LBM_EINVAL
+        assert lbm.lbm_tau1_batch_step(B.b, -1) == lbm.LBM_EINVAL
+        assert B.live == 1
+        B.step(3)
+        B.release(s)
+        assert lbm.lbm_tau1_batch_release(B.b, s) == lbm.LBM_EINVAL
+        assert B.live == 0
+        B.step(5)  # nothing live: no work
