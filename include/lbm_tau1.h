@@ -62,6 +62,12 @@ typedef enum { LBM_D3Q19 = 19, LBM_D3Q27 = 27 } lbm_lattice;
  * times a power-of-two scale in 16 bits and compute in FP32. */
 typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16S = 2, LBM_BF16S = 3 } lbm_storage;
 
+/* DENSE: state records for every node of the box. SPARSE: state records for
+ * the fluid nodes only, in a list numbered in box order, with an int32 table
+ * of the list index of each link's source (-1 for a wall); the list and the
+ * table are built by set_geometry (4 (q-1) + 4 bytes per fluid node). The
+ * sparse layout is for the Tau1 scheme, boxes of fewer than 2^31 nodes; its
+ * FP32 and FP64 results equal the dense kernels' bits. */
 typedef enum { LBM_DENSE = 0, LBM_SPARSE = 1 } lbm_layout;
 
 /* LBM_SCHEME_TAU1 is the method. LBM_SCHEME_BGK is the standard pull BGK at
