@@ -10,13 +10,11 @@
 // arguments, read from the device table. Everything that changes from step to
 // step lives in the table on the device: which copy holds a box's current
 // state, its step count (the stochastic-rounding seed), its 16-bit scales.
-// Boxes are stepped by one of three instances of the kernel, each with a work
-// table of its own and one launch per step: staged (TMA) tile columns through
-// the box's tensor maps (one per state copy, in device memory; the stage
-// mbarriers are set up once per launch and their phases run on from item to
-// item) for boxes of full tiles; the staged form with ragged-tile handling for
-// other boxes; and register tile columns where a box row of records cannot
-// start on 16 bytes (16-bit records, odd nx). A launch therefore has the same arguments every step, and K steps can be
+// Boxes whose tiles are all full are stepped by a staged (TMA) instance of
+// the kernel through their own tensor maps (one per state copy, in device
+// memory; the stage mbarriers are set up once per launch and their phases run
+// on from item to item), the others by a register instance: two work tables,
+// one launch each per step. A launch therefore has the same arguments every step, and K steps can be
 // captured once in a CUDA graph and replayed while boxes come and go (the
 // host edits the table between replays).
 //
@@ -75,7 +73,7 @@ __device__ void finish_box(BatchDomain& R, int storage)
     R.step = step;
 }
 
-template <int Q, int ST, int H, int MINB, int KIND>
+template <int Q, int ST, int H, int MINB, bool TMA>
 __global__ void __launch_bounds__(32 * H, MINB) tau1_batch_kernel(BatchTable* T)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -85,7 +83,6 @@ __global__ void __launch_bounds__(32 * H, MINB) tau1_batch_kernel(BatchTable* T)
     constexpr bool AMAX = ST == ST_F16S;
     const int nitems = T->nitems, ndom = T->ndom, chunk = T->chunk;
     const int* __restrict__ begin = T->item_begin;
-    constexpr bool TMA = KIND != BATCH_REGISTER;
     if constexpr (TMA) stage_init<Q, ST, H>(smem_raw);  // visible after the first item's barrier
     uint32_t phase = 0;
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
@@ -112,8 +109,7 @@ __global__ void __launch_bounds__(32 * H, MINB) tau1_batch_kernel(BatchTable* T)
         float amax[4] = {0.f, 0.f, 0.f, 0.f};
         __syncthreads();  // the previous item's last shared-memory reads are done
         if constexpr (TMA)
-            tile_column<Q, ST, H, AMAX, true, KIND == BATCH_STAGED_RAGGED>(a, sc, x0, y0, z0, z1, smem_raw, amax,
-                                                                           T->maps + 2 * slot + c, &phase);
+            tile_column<Q, ST, H, AMAX, true>(a, sc, x0, y0, z0, z1, smem_raw, amax, T->maps + 2 * slot + c, &phase);
         else
             tile_column<Q, ST, H, AMAX, false>(a, sc, x0, y0, z0, z1, smem_raw, amax);
         if (AMAX && (R.step + 1) % BATCH_RESCALE_EVERY == 0) {
@@ -139,13 +135,13 @@ __global__ void __launch_bounds__(32 * H, MINB) tau1_batch_kernel(BatchTable* T)
     if (threadIdx.x == 0) T->done = 0;
 }
 
-template <int Q, int ST, int V, int KIND>
+template <int Q, int ST, int V, bool TMA>
 struct BatchKernel {
     using E = typename Storage<ST>::ctype;
     static constexpr int H = Shape<Q, E, V>::H;
     using C = TCfg<Q, 32, H, E>;
-    static constexpr size_t SMEM = tile_smem<Q, ST, H, KIND != BATCH_REGISTER>();
-    static constexpr auto fn() { return tau1_batch_kernel<Q, ST, H, Shape<Q, E, V>::MINB, KIND>; }
+    static constexpr size_t SMEM = tile_smem<Q, ST, H, TMA>();
+    static constexpr auto fn() { return tau1_batch_kernel<Q, ST, H, Shape<Q, E, V>::MINB, TMA>; }
     static cudaError_t prepare(int& grid, int& tile_h)
     {
         auto kern = fn();
@@ -167,7 +163,7 @@ struct BatchKernel {
     }
 };
 
-template <int Q, int ST, int KIND>
+template <int Q, int ST, bool TMA>
 cudaError_t dispatch_v(int variant, bool prep, BatchTable* T, int& grid, int& tile_h, cudaStream_t s)
 {
     auto go = [&](auto k) {
@@ -175,61 +171,52 @@ cudaError_t dispatch_v(int variant, bool prep, BatchTable* T, int& grid, int& ti
         return prep ? K::prepare(grid, tile_h) : K::launch(T, grid, s);
     };
     if constexpr (ST == ST_F64) {
-        return variant == 0 ? go(BatchKernel<Q, ST, 0, KIND>{}) : cudaErrorInvalidValue;
+        return variant == 0 ? go(BatchKernel<Q, ST, 0, TMA>{}) : cudaErrorInvalidValue;
     } else {
         switch (variant) {
-        case 0: return go(BatchKernel<Q, ST, 0, KIND>{});
-        case 1: return go(BatchKernel<Q, ST, 1, KIND>{});
-        case 2: return go(BatchKernel<Q, ST, 2, KIND>{});
-        case 3: return go(BatchKernel<Q, ST, 3, KIND>{});
+        case 0: return go(BatchKernel<Q, ST, 0, TMA>{});
+        case 1: return go(BatchKernel<Q, ST, 1, TMA>{});
+        case 2: return go(BatchKernel<Q, ST, 2, TMA>{});
+        case 3: return go(BatchKernel<Q, ST, 3, TMA>{});
         default: return cudaErrorInvalidValue;
         }
     }
 }
 
-template <int KIND>
+template <bool TMA>
 cudaError_t dispatch(int q, int storage, int variant, bool prep, BatchTable* T, int& grid, int& tile_h,
                      cudaStream_t s)
 {
     switch (q * 10 + storage) {
-    case 190 + ST_F64: return dispatch_v<19, ST_F64, KIND>(variant, prep, T, grid, tile_h, s);
-    case 190 + ST_F32: return dispatch_v<19, ST_F32, KIND>(variant, prep, T, grid, tile_h, s);
-    case 190 + ST_F16S: return dispatch_v<19, ST_F16S, KIND>(variant, prep, T, grid, tile_h, s);
-    case 190 + ST_BF16S: return dispatch_v<19, ST_BF16S, KIND>(variant, prep, T, grid, tile_h, s);
-    case 270 + ST_F64: return dispatch_v<27, ST_F64, KIND>(variant, prep, T, grid, tile_h, s);
-    case 270 + ST_F32: return dispatch_v<27, ST_F32, KIND>(variant, prep, T, grid, tile_h, s);
-    case 270 + ST_F16S: return dispatch_v<27, ST_F16S, KIND>(variant, prep, T, grid, tile_h, s);
-    case 270 + ST_BF16S: return dispatch_v<27, ST_BF16S, KIND>(variant, prep, T, grid, tile_h, s);
+    case 190 + ST_F64: return dispatch_v<19, ST_F64, TMA>(variant, prep, T, grid, tile_h, s);
+    case 190 + ST_F32: return dispatch_v<19, ST_F32, TMA>(variant, prep, T, grid, tile_h, s);
+    case 190 + ST_F16S: return dispatch_v<19, ST_F16S, TMA>(variant, prep, T, grid, tile_h, s);
+    case 190 + ST_BF16S: return dispatch_v<19, ST_BF16S, TMA>(variant, prep, T, grid, tile_h, s);
+    case 270 + ST_F64: return dispatch_v<27, ST_F64, TMA>(variant, prep, T, grid, tile_h, s);
+    case 270 + ST_F32: return dispatch_v<27, ST_F32, TMA>(variant, prep, T, grid, tile_h, s);
+    case 270 + ST_F16S: return dispatch_v<27, ST_F16S, TMA>(variant, prep, T, grid, tile_h, s);
+    case 270 + ST_BF16S: return dispatch_v<27, ST_BF16S, TMA>(variant, prep, T, grid, tile_h, s);
     default: return cudaErrorInvalidValue;
     }
 }
 
 }  // namespace
 
-cudaError_t batch_kind_dispatch(int kind, int q, int storage, int variant, bool prep, BatchTable* T, int& grid,
-                                int& th, cudaStream_t s)
-{
-    switch (kind) {
-    case BATCH_REGISTER: return dispatch<BATCH_REGISTER>(q, storage, variant, prep, T, grid, th, s);
-    case BATCH_STAGED: return dispatch<BATCH_STAGED>(q, storage, variant, prep, T, grid, th, s);
-    case BATCH_STAGED_RAGGED: return dispatch<BATCH_STAGED_RAGGED>(q, storage, variant, prep, T, grid, th, s);
-    default: return cudaErrorInvalidValue;
-    }
-}
-
-cudaError_t batch_prepare(int q, int storage, int variant, int kind, int* grid, int* tile_h)
+cudaError_t batch_prepare(int q, int storage, int variant, bool tma, int* grid, int* tile_h)
 {
     int g = 0, th = 0;
-    cudaError_t e = batch_kind_dispatch(kind, q, storage, variant, true, nullptr, g, th, nullptr);
+    cudaError_t e = tma ? dispatch<true>(q, storage, variant, true, nullptr, g, th, nullptr)
+                        : dispatch<false>(q, storage, variant, true, nullptr, g, th, nullptr);
     *grid = g;
     *tile_h = th;
     return e;
 }
 
-cudaError_t launch_tau1_batch(int q, int storage, int variant, int kind, BatchTable* T, int grid, cudaStream_t s)
+cudaError_t launch_tau1_batch(int q, int storage, int variant, bool tma, BatchTable* T, int grid, cudaStream_t s)
 {
     int th = 0;
-    return batch_kind_dispatch(kind, q, storage, variant, false, T, grid, th, s);
+    return tma ? dispatch<true>(q, storage, variant, false, T, grid, th, s)
+               : dispatch<false>(q, storage, variant, false, T, grid, th, s);
 }
 
 }  // namespace lbm

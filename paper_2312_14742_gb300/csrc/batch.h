@@ -19,7 +19,7 @@ struct BatchDomain {
     float scale[2][8];   // 16-bit: {S, 1/S} of the contents of buf[0], buf[1]
     unsigned amax[4];    // 16-bit: max |value| stored this step (float bits)
     float gfloor;        // 64 |g|_max, the floor of the headroom rule
-    int tma;             // instance that steps the box (BATCH_REGISTER, _STAGED, _STAGED_RAGGED)
+    int tma;             // 1: full tiles, stepped by the staged (TMA) tile column
 };
 
 // Header of a batch in device memory; the step kernel's only argument.
@@ -34,12 +34,9 @@ struct BatchTable {
     const CUtensorMap* maps; // [capacity][2] tensor maps of buf[0], buf[1] (boxes with tma)
 };
 
-// Instances of the batched kernel: register tile columns; staged (TMA) for
-// boxes of full tiles; staged with ragged-tile handling.
-enum : int { BATCH_REGISTER = 0, BATCH_STAGED = 1, BATCH_STAGED_RAGGED = 2, BATCH_KINDS = 3 };
-
-// Persistent grid size and tile height (2H) of a kernel variant and instance.
-cudaError_t batch_prepare(int q, int storage, int variant, int kind, int* grid, int* tile_h);
-cudaError_t launch_tau1_batch(int q, int storage, int variant, int kind, BatchTable* T, int grid, cudaStream_t s);
+// Persistent grid size and tile height (2H) of a kernel variant, in its
+// staged (tma) or register instance.
+cudaError_t batch_prepare(int q, int storage, int variant, bool tma, int* grid, int* tile_h);
+cudaError_t launch_tau1_batch(int q, int storage, int variant, bool tma, BatchTable* T, int grid, cudaStream_t s);
 
 }  // namespace lbm

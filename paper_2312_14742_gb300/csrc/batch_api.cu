@@ -38,7 +38,7 @@ struct Slot {
     uint64_t bytes = 0;
     int64_t steps = 0;
     int ntiles = 0;  // tiles per plane
-    int tma = 0;     // instance (and table) that steps the box: BATCH_*
+    int tma = 0;     // stepped by the staged instance (table 1), else table 0
 };
 
 uint64_t round256(uint64_t b) { return (b + 255) & ~(uint64_t)255; }
@@ -52,16 +52,17 @@ struct lbm_tau1_batch {
     cudaStream_t capture = nullptr;  // private stream for graph capture
     cudaEvent_t side_done = nullptr;
     std::vector<Slot> slots;
-    // one work table per kernel instance (BATCH_*), all indexing the same box records
-    BatchTable* dtable[BATCH_KINDS] = {};
+    // two work tables: [0] boxes stepped by the register instance, [1] by the
+    // staged (TMA) instance; both index the same box records
+    BatchTable* dtable[2] = {};
     BatchDomain* ddom = nullptr;
-    int* dlive[BATCH_KINDS] = {};
-    int* dbegin[BATCH_KINDS] = {};
-    bool nonempty[BATCH_KINDS] = {};
+    int* dlive[2] = {};
+    int* dbegin[2] = {};
+    bool nonempty[2] = {};
     CUtensorMap* dmaps = nullptr;  // [capacity][2]
     Stage ring[RING];
     int ring_pos = 0;
-    int grid[BATCH_KINDS] = {}, tile_h = 0;
+    int grid[2] = {}, tile_h = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     uint64_t budget = 0, used = 0;
@@ -134,7 +135,7 @@ int box_items(const Slot& s, int chunk) { return s.ntiles * ((s.cfg.nz + chunk -
 lbm_status upload_table(lbm_tau1_batch* b)
 {
     int nlive = 0;
-    for (int t = 0; t < BATCH_KINDS; ++t) {
+    for (int t = 0; t < 2; ++t) {
         int chunk = 32;
         for (; chunk > 4; chunk /= 2) {
             int64_t tot = 0;
@@ -194,20 +195,16 @@ lbm_status upload_table(lbm_tau1_batch* b)
 // One step of every live box: one launch per non-empty table.
 cudaError_t launch_step_tables(lbm_tau1_batch* b, cudaStream_t s)
 {
-    for (int t = 0; t < BATCH_KINDS; ++t)
+    for (int t = 1; t >= 0; --t)
         if (b->nonempty[t]) {
-            cudaError_t e = launch_tau1_batch(b->cfg.q, b->cfg.storage, b->cfg.variant, t, b->dtable[t], b->grid[t], s);
+            cudaError_t e = launch_tau1_batch(b->cfg.q, b->cfg.storage, b->cfg.variant, t == 1, b->dtable[t],
+                                              b->grid[t], s);
             if (e != cudaSuccess) return e;
         }
     return cudaSuccess;
 }
 
-int launches_per_step(const lbm_tau1_batch* b)
-{
-    int n = 0;
-    for (int t = 0; t < BATCH_KINDS; ++t) n += b->nonempty[t] ? 1 : 0;
-    return n;
-}
+int launches_per_step(const lbm_tau1_batch* b) { return (b->nonempty[0] ? 1 : 0) + (b->nonempty[1] ? 1 : 0); }
 
 lbm_status capture_graph(lbm_tau1_batch* b)
 {
@@ -249,7 +246,7 @@ void free_batch(lbm_tau1_batch* b)
         if (s.ev) { cudaEventSynchronize(s.ev); cudaEventDestroy(s.ev); }
         if (s.p) cudaFreeHost(s.p);
     }
-    for (int t = 0; t < BATCH_KINDS; ++t) {
+    for (int t = 0; t < 2; ++t) {
         if (b->dtable[t]) cudaFree(b->dtable[t]);
         if (b->dlive[t]) cudaFree(b->dlive[t]);
         if (b->dbegin[t]) cudaFree(b->dbegin[t]);
@@ -311,13 +308,12 @@ lbm_status lbm_tau1_batch_create(const lbm_tau1_batch_config* cfg, lbm_tau1_batc
     b->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
     b->slots.resize((size_t)cfg->capacity);
     const int cap = cfg->capacity;
-    cudaError_t e = cudaSuccess;
-    for (int t = 0; t < BATCH_KINDS && e == cudaSuccess; ++t)
-        e = batch_prepare(cfg->q, cfg->storage, cfg->variant, t, &b->grid[t], &b->tile_h);
+    cudaError_t e = batch_prepare(cfg->q, cfg->storage, cfg->variant, false, &b->grid[0], &b->tile_h);
+    if (e == cudaSuccess) e = batch_prepare(cfg->q, cfg->storage, cfg->variant, true, &b->grid[1], &b->tile_h);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->side_done, cudaEventDisableTiming);
-    for (int t = 0; t < BATCH_KINDS; ++t) {
+    for (int t = 0; t < 2; ++t) {
         if (e == cudaSuccess) e = cudaMalloc(&b->dtable[t], sizeof(BatchTable));
         if (e == cudaSuccess) e = cudaMalloc(&b->dlive[t], (size_t)cap * sizeof(int));
         if (e == cudaSuccess) e = cudaMalloc(&b->dbegin[t], (size_t)cap * sizeof(int));
@@ -431,22 +427,20 @@ lbm_status lbm_tau1_batch_admit(lbm_tau1_batch* b, const lbm_tau1_config* cfg, c
             rec.scale[c][4 + f] = 1.0f / sc[f];
         }
     rec.gfloor = (float)(64.0 * gmax);
-    // staged tile columns (full-tile or ragged form) wherever a box row of
-    // records starts on 16 bytes (16-bit records: even nx), else register ones
+    // staged tile columns for boxes of full tiles (16-bit rows start on 16 bytes only for even nx)
     CUtensorMap maps[2];
-    const bool aligned = !((cfg->storage == LBM_F16S || cfg->storage == LBM_BF16S) && cfg->nx % 2 != 0);
-    const bool full = cfg->nx % 32 == 0 && cfg->ny % b->tile_h == 0;
-    rec.tma = !aligned ? BATCH_REGISTER : (full ? BATCH_STAGED : BATCH_STAGED_RAGGED);
-    for (int c = 0; c < 2 && rec.tma != BATCH_REGISTER; ++c)
+    rec.tma = cfg->nx % 32 == 0 && cfg->ny % b->tile_h == 0 &&
+              !((cfg->storage == LBM_F16S || cfg->storage == LBM_BF16S) && cfg->nx % 2 != 0);
+    for (int c = 0; c < 2 && rec.tma; ++c)
         if (encode_state_map(cfg->storage, s.buf[c], cfg->nx, cfg->ny, cfg->nz, b->tile_h + 2, &maps[c]) !=
             cudaSuccess)
-            rec.tma = BATCH_REGISTER;
+            rec.tma = 0;
     Stage* st = nullptr;
     BCUDA(b, stage_get(b, sizeof(rec) + sizeof(maps), &st), "batch_admit: staging buffer");
     std::memcpy(st->p, maps, sizeof(maps));
     std::memcpy(static_cast<unsigned char*>(st->p) + sizeof(maps), &rec, sizeof(rec));
     BCUDA(b, cudaStreamWaitEvent(b->stream, b->side_done, 0), "batch_admit: wait");
-    if (rec.tma != BATCH_REGISTER)
+    if (rec.tma)
         BCUDA(b, cudaMemcpyAsync(b->dmaps + 2 * id, st->p, sizeof(maps), cudaMemcpyHostToDevice, b->stream),
               "batch_admit: tensor map copy");
     BCUDA(b, cudaMemcpyAsync(b->ddom + id, static_cast<unsigned char*>(st->p) + sizeof(maps), sizeof(rec),

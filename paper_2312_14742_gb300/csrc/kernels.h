@@ -14,8 +14,7 @@ cudaError_t launch_tau1_simple(int q, int storage, const StepArgs& a, cudaStream
 cudaError_t launch_tau1_tiled(int q, int storage, int variant, const StepArgs& a, cudaStream_t s);
 bool tau1_tiled_supported(int q, int storage, int64_t n);
 int tau1_tiled_variants(int q, int storage);
-// Staged (TMA) form of the tiled kernel: same bits; every box whose rows of
-// records start on 16 bytes (16-bit storage: even nx).
+// Staged (TMA) form of the tiled kernel: same bits; for boxes with full tiles.
 bool tau1_tiled_tma_ok(int q, int storage, int variant, const StepArgs& a);
 cudaError_t launch_tau1_tiled_tma(int q, int storage, int variant, const StepArgs& a, cudaStream_t s);
 // Tensor map of a state copy for the staged kernels: 3D {4 nx, ny, nz} values,

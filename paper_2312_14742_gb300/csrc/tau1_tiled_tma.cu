@@ -3,12 +3,12 @@
 // tensor unit (cp.async.bulk.tensor), two planes ahead of its use, instead of
 // per-thread global loads held in registers across the plane barrier.
 //
-// Boxes whose tiles are all full (nx a multiple of 32, ny of the tile height)
-// run an instance for full tiles; other boxes run an instance that also
-// handles a ragged last tile (its nodes beyond the box, like halo nodes
-// outside it, come back zero-filled from the copy and are read from global
-// memory as periodic images, or are walls). The ragged handling costs 6% on
-// full tiles, so the two are separate instances.
+// It serves boxes whose tiles are all full (nx a multiple of 32, ny of the
+// tile height), so every tile lies inside the box; halo nodes outside it come
+// back zero-filled from the copy and are read from global memory (periodic
+// images, which the copy cannot wrap) or are walls. Ragged boxes use the
+// register form: handling a ragged last tile here, even behind a block-uniform
+// branch, cost 6% on full tiles.
 // The state is viewed as a 3D array of 4 nx x ny x nz values (one record is
 // 4 values), so that a box row of 34 records starts at an element coordinate
 // that is a multiple of 4 values: a multiple of 16 bytes for every format.
@@ -22,7 +22,7 @@ namespace {
 
 using namespace tile;
 
-template <int Q, int ST, int H, int MINB, bool RAGGED>
+template <int Q, int ST, int H, int MINB>
 __global__ void __launch_bounds__(32 * H, MINB)
     tau1_tiled_tma_kernel(StepArgs a, int ntx, int ntiles, int chunk, const __grid_constant__ CUtensorMap tmap)
 {
@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(32 * H, MINB)
     stage_init<Q, ST, H>(smem_raw);
     __syncthreads();
     uint32_t phase = 0;
-    tile_column<Q, ST, H, false, true, RAGGED>(a, sc, x0, y0, z0, z1, smem_raw, amax, &tmap, &phase);
+    tile_column<Q, ST, H, false, true>(a, sc, x0, y0, z0, z1, smem_raw, amax, &tmap, &phase);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
@@ -91,14 +91,12 @@ cudaError_t launch_t(const StepArgs& a, cudaStream_t s)
     constexpr int H = Shape<Q, E, V>::H;
     constexpr size_t SMEM = tile_smem<Q, ST, H, true>();
     static_assert(SMEM <= 227 * 1024, "shared memory of one block");
-    const bool ragged = a.nx % 32 != 0 || a.ny % (2 * H) != 0;
-    auto kern = ragged ? tau1_tiled_tma_kernel<Q, ST, H, Shape<Q, E, V>::MINB, true>
-                       : tau1_tiled_tma_kernel<Q, ST, H, Shape<Q, E, V>::MINB, false>;
-    static bool attr_set[2] = {false, false};
-    if (!attr_set[ragged]) {
+    auto kern = tau1_tiled_tma_kernel<Q, ST, H, Shape<Q, E, V>::MINB>;
+    static bool attr_set = false;
+    if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
         if (e != cudaSuccess) return e;
-        attr_set[ragged] = true;
+        attr_set = true;
     }
     CUtensorMap map;
     cudaError_t e = encode_state<ST>(&map, a, 2 * H + 2);
@@ -133,9 +131,8 @@ cudaError_t launch_v(int variant, const StepArgs& a, cudaStream_t s)
 
 bool tau1_tiled_tma_ok(int q, int storage, int variant, const StepArgs& a)
 {
-    if (tile_height(q, storage, variant) == 0) return false;
-    // a box row of 16-bit records starts on 16 bytes only if nx is even
-    if ((storage == ST_F16S || storage == ST_BF16S) && a.nx % 2 != 0) return false;
+    const int th = tile_height(q, storage, variant);
+    if (th == 0 || a.nx % 32 != 0 || a.ny % th != 0) return false;
     // a box row of 16-bit records starts at a multiple of 16 bytes only if nx is even
     if ((storage == ST_F16S || storage == ST_BF16S) && a.nx % 2 != 0) return false;
     if ((reinterpret_cast<uintptr_t>(a.pre) & 15) != 0) return false;

@@ -214,11 +214,9 @@ __device__ __forceinline__ void track_amax(float (&m)[4], E d, E ux, E uy, E uz)
 // thread stores. With TMA the raw records come from shared-memory stages
 // (initialised by stage_init; *phase_io carries their phase bits from call
 // to call) filled by the tensor unit through tmap (the state read, viewed as a 3D
-// array of 4 nx x ny x nz values). Halo nodes outside the box are read from
-// global memory (periodic images) or are walls. Without RAGGED the tile must
-// lie inside the box; with RAGGED its nodes beyond the box are handled the
-// same way (a form for ragged boxes, measured 6% slower on full tiles).
-template <int Q, int ST, int H, bool AMAX, bool TMA = false, bool RAGGED = false>
+// array of 4 nx x ny x nz values); the tile must lie inside the box, and halo
+// nodes outside it are read from global memory (periodic images) or are walls.
+template <int Q, int ST, int H, bool AMAX, bool TMA = false>
 __device__ __forceinline__ void tile_column(const StepArgs& a, const Scales& sc, int x0, int y0, int z0, int z1,
                                             unsigned char* smem_raw, float (&amax)[4],
                                             const CUtensorMap* tmap = nullptr, uint32_t* phase_io = nullptr)
@@ -337,22 +335,8 @@ __device__ __forceinline__ void tile_column(const StepArgs& a, const Scales& sc,
         phase ^= 1u << st;
         const unsigned char* base = stages + st * SC::STAGE_BYTES;
         auto cell = [&](int c, int r) { return base + (size_t)(r * SC::SW + c) * SC::REC; };
-        if constexpr (RAGGED) {
-            // tile nodes beyond the box (a ragged last tile) are periodic images or walls
-            if (activeA)
-                S::load_at(cell(tx + SC::XOFF, ty + 1), sc.inv, r_own.d.v.x, r_own.ux.v.x, r_own.uy.v.x, r_own.uz.v.x);
-            else
-                load_node<ST>(a, sc, okA, zoff + xyA, r_own.d.v.x, r_own.ux.v.x, r_own.uy.v.x, r_own.uz.v.x);
-            if (activeB)
-                S::load_at(cell(tx + SC::XOFF, ty + H + 1), sc.inv, r_own.d.v.y, r_own.ux.v.y, r_own.uy.v.y,
-                           r_own.uz.v.y);
-            else
-                load_node<ST>(a, sc, okB, zoff + xyB, r_own.d.v.y, r_own.ux.v.y, r_own.uy.v.y, r_own.uz.v.y);
-        } else {
-            S::load_at(cell(tx + SC::XOFF, ty + 1), sc.inv, r_own.d.v.x, r_own.ux.v.x, r_own.uy.v.x, r_own.uz.v.x);
-            S::load_at(cell(tx + SC::XOFF, ty + H + 1), sc.inv, r_own.d.v.y, r_own.ux.v.y, r_own.uy.v.y,
-                       r_own.uz.v.y);
-        }
+        S::load_at(cell(tx + SC::XOFF, ty + 1), sc.inv, r_own.d.v.x, r_own.ux.v.x, r_own.uy.v.x, r_own.uz.v.x);
+        S::load_at(cell(tx + SC::XOFF, ty + H + 1), sc.inv, r_own.d.v.y, r_own.ux.v.y, r_own.uy.v.y, r_own.uz.v.y);
         if (has_halo) {
             if (hinA) S::load_at(cell(hcA, hrA), sc.inv, r_halo.d.v.x, r_halo.ux.v.x, r_halo.uy.v.x, r_halo.uz.v.x);
             else load_node<ST>(a, sc, hokA, zoff + hxyA, r_halo.d.v.x, r_halo.ux.v.x, r_halo.uy.v.x, r_halo.uz.v.x);
