@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -102,6 +103,9 @@ __device__ __forceinline__ uint32_t sr_bits(uint32_t i, uint32_t seed)
 template <typename H> struct Storage16 {
     using ctype = float;
     static constexpr int NODE_BYTES = 8;
+    // BF16 has the FP32 exponent range and always keeps S_f = 1: no scaling
+    static constexpr bool SCALED = !std::is_same<H, __nv_bfloat16>::value;
+    __device__ static __forceinline__ float sc_mul(float v, float s) { return SCALED ? v * s : v; }
     __device__ static __forceinline__ float to_f(H h);
     __device__ static __forceinline__ H from_f(float f);
     __device__ static __forceinline__ uint32_t pack_sr(float lo, float hi, uint32_t r);
@@ -119,10 +123,10 @@ template <typename H> struct Storage16 {
     __device__ static __forceinline__ void decode(uint2 w, const float* inv, float& d, float& ux, float& uy, float& uz)
     {
         const H* h = reinterpret_cast<const H*>(&w);
-        d = to_f(h[0]) * inv[0];
-        ux = to_f(h[1]) * inv[1];
-        uy = to_f(h[2]) * inv[2];
-        uz = to_f(h[3]) * inv[3];
+        d = sc_mul(to_f(h[0]), inv[0]);
+        ux = sc_mul(to_f(h[1]), inv[1]);
+        uy = sc_mul(to_f(h[2]), inv[2]);
+        uz = sc_mul(to_f(h[3]), inv[3]);
     }
     // round to nearest
     __device__ static __forceinline__ void store(void* base, uint32_t i, float d, float ux, float uy, float uz,
@@ -130,10 +134,10 @@ template <typename H> struct Storage16 {
     {
         uint2 w;
         H* h = reinterpret_cast<H*>(&w);
-        h[0] = from_f(d * sc[0]);
-        h[1] = from_f(ux * sc[1]);
-        h[2] = from_f(uy * sc[2]);
-        h[3] = from_f(uz * sc[3]);
+        h[0] = from_f(sc_mul(d, sc[0]));
+        h[1] = from_f(sc_mul(ux, sc[1]));
+        h[2] = from_f(sc_mul(uy, sc[2]));
+        h[3] = from_f(sc_mul(uz, sc[3]));
         static_cast<uint2*>(base)[i] = w;
     }
     // stochastic rounding with bits from sr_bits(i, seed)
@@ -142,8 +146,8 @@ template <typename H> struct Storage16 {
     {
         const uint32_t r = sr_bits(i, seed);
         uint2 w;
-        w.x = pack_sr(d * sc[0], ux * sc[1], r);
-        w.y = pack_sr(uy * sc[2], uz * sc[3], r * 0x85EBCA6Bu + 0x165667B1u);
+        w.x = pack_sr(sc_mul(d, sc[0]), sc_mul(ux, sc[1]), r);
+        w.y = pack_sr(sc_mul(uy, sc[2]), sc_mul(uz, sc[3]), r * 0x85EBCA6Bu + 0x165667B1u);
         static_cast<uint2*>(base)[i] = w;
     }
 };
