@@ -201,3 +201,25 @@ def test_batch_error_paths():
         assert lbm.lbm_tau1_batch_release(B.b, s) == lbm.LBM_EINVAL
         assert B.live == 0
         B.step(5)  # nothing live: no work
+
+
+def test_poisoned_box_does_not_touch_its_neighbours():
+    """A box driven to divergence (g far too large) is reported by stats and
+    released; the other box of the batch keeps the bits it has alone."""
+    good, per, g = boxes(21)[0]
+    bad = boxes(21)[2][0]
+    with Batch(19, "f32", capacity=4, graph_steps=50) as A:
+        s = A.admit(good, per, g)
+        A.step(200)
+        alone = A.get_fields(s)
+    with Batch(19, "f32", capacity=4, graph_steps=50) as B:
+        s = B.admit(good, per, g)
+        x = B.admit(bad, (1, 1, 0), (0.2, 0.0, 0.0))
+        B.step(200)
+        st = B.stats([s, x], allow_diverged=True)
+        assert st[0]["nonfinite"] == 0 and st[0]["max_abs_u"] < 0.3
+        assert st[1]["nonfinite"] > 0 or st[1]["max_abs_u"] > 0.3
+        B.release(x)
+        mixed = B.get_fields(s)
+    for a, b in zip(alone, mixed):
+        assert np.array_equal(a, b)

@@ -205,3 +205,24 @@ def test_plain_server_is_first_come_first_served():
         assert b.admitted >= a.finished  # one at a time
     assert updates == sum(r.n_fluid * r.steps for r in res)
     assert serve.permeability_diff(res, res) == 0.0
+
+
+def test_a_diverged_request_is_released_and_the_rest_converge():
+    reqs = serve.make_requests(6, 91, edges=(32, 48))
+    clock = FakeClock()
+    fb = FakeBatch(clock, 10 ** 9, reqs)
+    poisoned = reqs[2]
+    real_stats = fb.stats
+
+    def stats(slots, allow_diverged=False):
+        out = real_stats(slots, allow_diverged)
+        for s, st in zip(slots, out):
+            if fb.live_boxes[s][0] is poisoned:
+                st["nonfinite"] = 7
+        return out
+    fb.stats = stats
+    srv = serve.BatchedServer(batch=fb, clock=clock, sleep=clock.sleep)
+    res = {r.id: r for r in srv.run(reqs, geometry_fn=fake_geometry, workers=0)}
+    assert res[poisoned.id].status == "diverged" and res[poisoned.id].steps == 100
+    assert all(r.status == "converged" for i, r in res.items() if i != poisoned.id)
+    assert fb.live == 0
