@@ -170,7 +170,9 @@ int64_t lbm_tau1_launch_count(const lbm_tau1* h);
 
 /* ---- Tile-shape autotuning (no counterpart in the paper, whose CPU kernels
  * fix the chunk shape at compile time, Section 3.2). The tiled kernel comes in
- * several tile-shape variants; the default is variant 0. */
+ * variants: a tile shape (tile height, resident blocks per SM) and the number
+ * of z planes a block steps (variants [0, n/2) step 24 planes per block,
+ * [n/2, n) 32, n = lbm_tau1_variant_count). The default is variant 0. */
 
 /* Number of variants of the handle's step kernel (1 if it has none). */
 int32_t lbm_tau1_variant_count(const lbm_tau1* h);
@@ -218,7 +220,7 @@ typedef struct lbm_tau1_batch lbm_tau1_batch;  /* opaque, owned by the library *
 typedef struct lbm_tau1_batch_config {
     int32_t q;            /* lbm_lattice of every box */
     int32_t storage;      /* lbm_storage of every box */
-    int32_t variant;      /* tile-shape variant of the tiled kernel (as lbm_tau1_set_variant) */
+    int32_t variant;      /* tile shape, 0 <= variant < lbm_tau1_variant_count of a tiled box / 2 */
     int32_t capacity;     /* most boxes live at once, >= 1 */
     int32_t graph_steps;  /* steps per captured graph (>= 1; 0 = 100) */
     int32_t reserved;

@@ -295,7 +295,7 @@ lbm_status lbm_tau1_batch_create(const lbm_tau1_batch_config* cfg, lbm_tau1_batc
     if (!cfg || !out) return bfail(nullptr, LBM_EINVAL, "batch_create: NULL argument");
     if (cfg->q != 19 && cfg->q != 27) return bfail(nullptr, LBM_EINVAL, "batch_create: q must be 19 or 27");
     if (cfg->storage < LBM_F64 || cfg->storage > LBM_BF16S) return bfail(nullptr, LBM_EINVAL, "batch_create: bad storage");
-    if (cfg->variant < 0 || cfg->variant >= tau1_tiled_variants(cfg->q, cfg->storage))
+    if (cfg->variant < 0 || cfg->variant >= tau1_tile_shapes(cfg->storage))
         return bfail(nullptr, LBM_EINVAL, "batch_create: bad variant");
     if (cfg->capacity < 1 || cfg->capacity > (1 << 20)) return bfail(nullptr, LBM_EINVAL, "batch_create: bad capacity");
     if (cfg->graph_steps < 0 || cfg->graph_steps > 100000)

@@ -13,7 +13,8 @@ namespace lbm {
 cudaError_t launch_tau1_simple(int q, int storage, const StepArgs& a, cudaStream_t s);
 cudaError_t launch_tau1_tiled(int q, int storage, int variant, const StepArgs& a, cudaStream_t s);
 bool tau1_tiled_supported(int q, int storage, int64_t n);
-int tau1_tiled_variants(int q, int storage);
+int tau1_tiled_variants(int q, int storage);  // tile shapes x z-chunk heights
+int tau1_tile_shapes(int storage);            // tile shapes (the batched kernel's variants)
 // Staged (TMA) form of the tiled kernel: same bits; for boxes with full tiles.
 bool tau1_tiled_tma_ok(int q, int storage, int variant, const StepArgs& a);
 cudaError_t launch_tau1_tiled_tma(int q, int storage, int variant, const StepArgs& a, cudaStream_t s);

@@ -85,7 +85,7 @@ template <int ST> cudaError_t encode_at(CUtensorMap* map, const void* base, int 
 }
 
 template <int Q, int ST, int V>
-cudaError_t launch_t(const StepArgs& a, cudaStream_t s)
+cudaError_t launch_t(const StepArgs& a, int zchunk, cudaStream_t s)
 {
     using E = typename Storage<ST>::ctype;
     constexpr int H = Shape<Q, E, V>::H;
@@ -103,7 +103,7 @@ cudaError_t launch_t(const StepArgs& a, cudaStream_t s)
     if (e != cudaSuccess) return e;
     const int ntx = (a.nx + 31) / 32;
     const int ntiles = ntx * ((a.ny + 2 * H - 1) / (2 * H));
-    const int chunk = a.nz < 32 ? a.nz : 32;
+    const int chunk = a.nz < zchunk ? a.nz : zchunk;
     const int nchunks = (a.nz + chunk - 1) / chunk;
     const long long blocks = (long long)ntiles * nchunks;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
@@ -114,14 +114,16 @@ cudaError_t launch_t(const StepArgs& a, cudaStream_t s)
 template <int Q, int ST>
 cudaError_t launch_v(int variant, const StepArgs& a, cudaStream_t s)
 {
+    if (variant < 0 || variant >= 2 * tile_shapes(ST)) return cudaErrorInvalidValue;
+    const int zchunk = variant_chunk(ST, variant);
     if constexpr (ST == ST_F64) {
-        return variant == 0 ? launch_t<Q, ST, 0>(a, s) : cudaErrorInvalidValue;
+        return launch_t<Q, ST, 0>(a, zchunk, s);
     } else {
-        switch (variant) {
-        case 0: return launch_t<Q, ST, 0>(a, s);
-        case 1: return launch_t<Q, ST, 1>(a, s);
-        case 2: return launch_t<Q, ST, 2>(a, s);
-        case 3: return launch_t<Q, ST, 3>(a, s);
+        switch (variant_shape(ST, variant)) {
+        case 0: return launch_t<Q, ST, 0>(a, zchunk, s);
+        case 1: return launch_t<Q, ST, 1>(a, zchunk, s);
+        case 2: return launch_t<Q, ST, 2>(a, zchunk, s);
+        case 3: return launch_t<Q, ST, 3>(a, zchunk, s);
         default: return cudaErrorInvalidValue;
         }
     }
