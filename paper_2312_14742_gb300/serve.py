@@ -12,6 +12,12 @@ chunk, and releases a sample as soon as it has converged. The plain server
 is the baseline: one sample at a time, each in its own single-box handle,
 first come first served.
 
+Admission also caps the live work: past about two waves of tile columns the
+GPU is saturated, and more live boxes only lengthen every box's step, so the
+batched server admits a box only while the live boxes hold at most
+`max_live_nodes` nodes (the first box is always admitted). Requests beyond the
+cap wait in arrival order.
+
 Convergence: after each chunk of 100 steps, |U - U_prev| < tol |U| with U
 the superficial mean u_x + g_x/2, or the step cap. With 16-bit storage the
 stored state carries stochastic-rounding noise, so the mean U of N_f fluid
@@ -157,7 +163,7 @@ class BatchedServer:
 
     def __init__(self, q: int = 19, storage: str = "f32", capacity: int = 256, chunk: int = 100, tol: float = 1e-6,
                  cap: int = 20000, g: float = 1e-5, hbm_budget: int = 0, variant: int = 0, batch=None,
-                 clock=time.perf_counter, sleep=time.sleep):
+                 clock=time.perf_counter, sleep=time.sleep, max_live_nodes: int | None = 2 ** 25):
         if batch is None:
             from .lbm import Batch
 
@@ -170,6 +176,7 @@ class BatchedServer:
         self.g = float(g)
         self.clock = clock
         self.sleep = sleep
+        self.max_live_nodes = max_live_nodes
         self.fluid_updates = 0
 
     def run(self, requests: list[Request], geometry_fn=geometry, prefetch: int = 8, workers: int = 4) -> list[Result]:
@@ -186,8 +193,11 @@ class BatchedServer:
                 while nxt < len(order) and order[nxt].arrival <= now:
                     queue.append((nxt, order[nxt], None))
                     nxt += 1
+                live_nodes = sum(v[0].edge ** 3 for v in live.values())
                 while queue:
                     k, req, mask = queue[0]
+                    if live and self.max_live_nodes and live_nodes + req.edge ** 3 > self.max_live_nodes:
+                        break
                     if mask is None:
                         mask = pre.get(k, req)
                         queue[0] = (k, req, mask)
@@ -198,6 +208,7 @@ class BatchedServer:
                         break
                     queue.popleft()
                     live[slot] = (req, None, self.clock() - t0, 0)
+                    live_nodes += req.edge ** 3
                 if not live:
                     if nxt < len(order):
                         self.sleep(max(0.0, order[nxt].arrival - (self.clock() - t0)))
@@ -306,21 +317,26 @@ def calibrate(requests: list[Request], **server_kw) -> float:
 
 def compare(n: int, seed: int, edges=EDGES, storages=("f32", "f16s"), load: float = 0.8, calib: int = 16,
             tol: float = 1e-6, cap: int = 20000, capacity: int = 256, q: int = 19, g: float = 1e-5,
-            plain: bool = True) -> dict:
+            plain: bool = True, rate: float | None = None, max_live_nodes: int | None = 2 ** 25) -> dict:
     """The serving comparison: Poisson arrivals at `load` times the batched
-    FP32 capacity (measured on `calib` requests of the same stream), served
-    batched in each storage format and plain (one at a time, FP32)."""
+    FP32 capacity (measured on `calib` requests of the same stream; or at a
+    given `rate`), served batched in each storage format and plain (one at a
+    time, FP32)."""
     reqs = make_requests(n, seed, edges)
-    cap_rps = calibrate(reqs[:calib], q=q, storage="f32", capacity=capacity, tol=tol, cap=cap, g=g)
-    rate = load * cap_rps
+    cap_rps = None
+    if rate is None:
+        cap_rps = calibrate(reqs[:calib], q=q, storage="f32", capacity=capacity, tol=tol, cap=cap, g=g,
+                            max_live_nodes=max_live_nodes)
+        rate = load * cap_rps
     arr = poisson_arrivals(n, rate, seed)
     for r, a in zip(reqs, arr):
         r.arrival = float(a)
     out = {"requests": n, "seed": seed, "edges": [int(e) for e in edges], "calibration_requests_per_s": cap_rps,
-           "arrival_rate_per_s": rate, "load": load, "chunk": 100, "tol": tol, "cap": cap}
+           "arrival_rate_per_s": rate, "load": load, "chunk": 100, "tol": tol, "cap": cap,
+           "max_live_nodes": max_live_nodes}
     res = {}
     for st in storages:
-        srv = BatchedServer(q=q, storage=st, capacity=capacity, tol=tol, cap=cap, g=g)
+        srv = BatchedServer(q=q, storage=st, capacity=capacity, tol=tol, cap=cap, g=g, max_live_nodes=max_live_nodes)
         try:
             r = srv.run(reqs)
         finally:
@@ -345,10 +361,13 @@ def main(argv=None) -> int:
     ap.add_argument("--calib", type=int, default=32)
     ap.add_argument("--storages", default="f32,f16s")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--rate", type=float, default=None, help="arrival rate (1/s) instead of calibrating")
+    ap.add_argument("--max-live-nodes", type=int, default=2 ** 25, help="cap on live box nodes (0: none)")
     ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)
     edges = tuple(e for e in EDGES if e <= a.max_edge)
-    res = compare(a.requests, a.seed, edges, tuple(a.storages.split(",")), a.load, a.calib, plain=not a.no_plain)
+    res = compare(a.requests, a.seed, edges, tuple(a.storages.split(",")), a.load, a.calib, plain=not a.no_plain,
+                  rate=a.rate, max_live_nodes=a.max_live_nodes or None)
     line = json.dumps(res)
     print(line)
     if a.out:

@@ -226,3 +226,25 @@ def test_a_diverged_request_is_released_and_the_rest_converge():
     assert res[poisoned.id].status == "diverged" and res[poisoned.id].steps == 100
     assert all(r.status == "converged" for i, r in res.items() if i != poisoned.id)
     assert fb.live == 0
+
+
+def test_live_work_cap():
+    """With a cap on live nodes, no more than the cap is ever live (except a
+    single box larger than it), and every request is still served in order."""
+    reqs = serve.make_requests(30, 17, edges=(32, 64, 96))
+    for r in reqs:
+        r.arrival = 0.0
+    clock = FakeClock()
+    fb = FakeBatch(clock, 10 ** 12, reqs)
+    peak = [0]
+    real_step = fb.step
+
+    def step(n):
+        peak[0] = max(peak[0], sum(b[0].edge ** 3 for b in fb.live_boxes.values()))
+        real_step(n)
+    fb.step = step
+    cap = 2 * 96 ** 3
+    srv = serve.BatchedServer(batch=fb, clock=clock, sleep=clock.sleep, max_live_nodes=cap)
+    res = srv.run(reqs, geometry_fn=fake_geometry, workers=0)
+    assert len(res) == 30 and peak[0] <= cap
+    assert fb.admit_order == list(range(30))
