@@ -26,8 +26,18 @@ struct f2 {
 __device__ __forceinline__ f2 operator+(f2 a, f2 b) { return f2(__fadd2_rn(a.v, b.v)); }
 __device__ __forceinline__ f2 operator*(f2 a, f2 b) { return f2(__fmul2_rn(a.v, b.v)); }
 __device__ __forceinline__ f2 fma(f2 a, f2 b, f2 c) { return f2(__ffma2_rn(a.v, b.v, c.v)); }
-// a - b as b * (-1) + a: the product is exact, so this rounds like a - b
-__device__ __forceinline__ f2 operator-(f2 a, f2 b) { return f2(__ffma2_rn(b.v, make_float2(-1.f, -1.f), a.v)); }
+// packed subtraction (sub.rn.f32x2): one IEEE rounding per lane like scalar
+// a - b, and no register pair of -1 constants to keep or rebuild
+__device__ __forceinline__ f2 operator-(f2 a, f2 b)
+{
+    unsigned long long ra, rb, rd;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(ra) : "f"(a.v.x), "f"(a.v.y));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(rb) : "f"(b.v.x), "f"(b.v.y));
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
+    f2 d;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(d.v.x), "=f"(d.v.y) : "l"(rd));
+    return d;
+}
 __device__ __forceinline__ f2 operator-(f2 a) { return f2(__fmul2_rn(a.v, make_float2(-1.f, -1.f))); }
 __device__ __forceinline__ f2& operator+=(f2& a, f2 b) { a = a + b; return a; }
 __device__ __forceinline__ f2& operator-=(f2& a, f2 b) { a = a - b; return a; }
