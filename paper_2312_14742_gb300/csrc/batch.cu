@@ -6,17 +6,22 @@
 // planes high; the host lowers the chunk (32 down to 4 planes) when few boxes
 // are live, so that a step spreads over the SMs and its latency, one column,
 // stays short. A node's result does not depend on the chunk. A grid of (SMs x resident
-// blocks) walks the list; each item is one tile_column() call with that box's
-// arguments, read from the device table. Everything that changes from step to
+// blocks) works through the list: each block takes its first item by its
+// index and then the next unclaimed one (an atomic counter), so blocks that
+// drew small items (partial tiles or chunks, small boxes) take more of them.
+// Each item is one tile_column() call with that box's arguments, read from the
+// device table. Everything that changes from step to
 // step lives in the table on the device: which copy holds a box's current
 // state, its step count (the stochastic-rounding seed), its 16-bit scales.
 // Boxes whose tiles are all full are stepped by a staged (TMA) instance of
 // the kernel through their own tensor maps (one per state copy, in device
 // memory; the stage mbarriers are set up once per launch and their phases run
 // on from item to item), the others by a register instance: two work tables,
-// one launch each per step. A launch therefore has the same arguments every step, and K steps can be
-// captured once in a CUDA graph and replayed while boxes come and go (the
-// host edits the table between replays).
+// one launch each per step. A launch therefore has the same arguments every
+// step, and K steps can be captured once in a CUDA graph and replayed while
+// boxes come and go (the host edits the table between replays). The two
+// tables hold different boxes, so the graph holds them as two independent
+// chains of K launches that run side by side.
 //
 // The last block to finish (an atomic count, no waiting) closes the step for
 // every live box: swaps its copies, counts the step and, for FP16 storage,
@@ -85,7 +90,10 @@ __global__ void __launch_bounds__(32 * H, MINB) tau1_batch_kernel(BatchTable* T)
     const int* __restrict__ begin = T->item_begin;
     if constexpr (TMA) stage_init<Q, ST, H>(smem_raw);  // visible after the first item's barrier
     uint32_t phase = 0;
-    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    __shared__ int next_item;
+    // each block takes its first item by its index, then the next free one
+    // (items differ in size: partial tiles, partial chunks, several boxes)
+    for (int it = blockIdx.x; it < nitems;) {
         // box of this item: the last d with begin[d] <= it
         int lo = 0, hi = ndom - 1;
         while (lo < hi) {
@@ -121,6 +129,9 @@ __global__ void __launch_bounds__(32 * H, MINB) tau1_batch_kernel(BatchTable* T)
                 if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(&R.amax[f], __float_as_uint(m));
             }
         }
+        if (threadIdx.x == 0) next_item = (int)gridDim.x + (int)atomicAdd(&T->next, 1u);
+        __syncthreads();
+        it = next_item;
     }
     // close the step: the last block to arrive updates every live box
     __syncthreads();
@@ -132,7 +143,10 @@ __global__ void __launch_bounds__(32 * H, MINB) tau1_batch_kernel(BatchTable* T)
     if (!last) return;
     __threadfence();
     for (int d = threadIdx.x; d < ndom; d += blockDim.x) finish_box(T->dom[T->live[d]], ST);
-    if (threadIdx.x == 0) T->done = 0;
+    if (threadIdx.x == 0) {
+        T->done = 0;
+        T->next = 0;
+    }
 }
 
 template <int Q, int ST, int V, bool TMA>

@@ -27,6 +27,7 @@ struct BatchTable {
     int nitems;              // work items (tile columns) of all live boxes
     int ndom;                // live boxes
     unsigned done;           // blocks finished in the current step
+    unsigned next;           // items handed out beyond the first one of each block
     int chunk;               // planes per work item (the same for every box)
     const int* live;         // [ndom] slot of each live box
     const int* item_begin;   // [ndom] first item of each live box

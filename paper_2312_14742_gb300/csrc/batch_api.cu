@@ -50,6 +50,8 @@ struct lbm_tau1_batch {
     cudaStream_t stream = nullptr;   // the caller's stream: all steps and table edits
     cudaStream_t side = nullptr;     // admission uploads (mask copy, flags, state init)
     cudaStream_t capture = nullptr;  // private stream for graph capture
+    cudaStream_t capture2 = nullptr; // second capture branch: the other table's chain
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     cudaEvent_t side_done = nullptr;
     std::vector<Slot> slots;
     // two work tables: [0] boxes stepped by the register instance, [1] by the
@@ -156,6 +158,7 @@ lbm_status upload_table(lbm_tau1_batch* b)
         hdr.nitems = items;
         hdr.ndom = nd;
         hdr.done = 0;
+        hdr.next = 0;
         hdr.chunk = chunk;
         hdr.live = b->dlive[t];
         hdr.item_begin = b->dbegin[t];
@@ -211,7 +214,21 @@ lbm_status capture_graph(lbm_tau1_batch* b)
     const int k = b->cfg.graph_steps;
     BCUDA(b, cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal), "batch: begin capture");
     cudaError_t le = cudaSuccess;
-    for (int i = 0; i < k && le == cudaSuccess; ++i) le = launch_step_tables(b, b->capture);
+    if (b->nonempty[0] && b->nonempty[1]) {
+        // the two tables hold different boxes: two independent chains of k
+        // steps, which the GPU runs side by side (one fills the other's tails)
+        le = cudaEventRecord(b->fork_ev, b->capture);
+        if (le == cudaSuccess) le = cudaStreamWaitEvent(b->capture2, b->fork_ev, 0);
+        for (int t = 1; t >= 0; --t) {
+            cudaStream_t cs = t == 1 ? b->capture : b->capture2;
+            for (int i = 0; i < k && le == cudaSuccess; ++i)
+                le = launch_tau1_batch(b->cfg.q, b->cfg.storage, b->cfg.variant, t == 1, b->dtable[t], b->grid[t], cs);
+        }
+        if (le == cudaSuccess) le = cudaEventRecord(b->join_ev, b->capture2);
+        if (le == cudaSuccess) le = cudaStreamWaitEvent(b->capture, b->join_ev, 0);
+    } else {
+        for (int i = 0; i < k && le == cudaSuccess; ++i) le = launch_step_tables(b, b->capture);
+    }
     cudaGraph_t g = nullptr;
     cudaError_t ee = cudaStreamEndCapture(b->capture, &g);
     if (le != cudaSuccess || ee != cudaSuccess) {
@@ -259,6 +276,9 @@ void free_batch(lbm_tau1_batch* b)
     if (b->side_done) cudaEventDestroy(b->side_done);
     if (b->side) cudaStreamDestroy(b->side);
     if (b->capture) cudaStreamDestroy(b->capture);
+    if (b->capture2) cudaStreamDestroy(b->capture2);
+    if (b->fork_ev) cudaEventDestroy(b->fork_ev);
+    if (b->join_ev) cudaEventDestroy(b->join_ev);
 }
 
 lbm_status live_slot(lbm_tau1_batch* b, int32_t slot, const char* what)
@@ -312,6 +332,9 @@ lbm_status lbm_tau1_batch_create(const lbm_tau1_batch_config* cfg, lbm_tau1_batc
     if (e == cudaSuccess) e = batch_prepare(cfg->q, cfg->storage, cfg->variant, true, &b->grid[1], &b->tile_h);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture2, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join_ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->side_done, cudaEventDisableTiming);
     for (int t = 0; t < 2; ++t) {
         if (e == cudaSuccess) e = cudaMalloc(&b->dtable[t], sizeof(BatchTable));
