@@ -137,7 +137,10 @@ lbm_status lbm_tau1_set_fields(lbm_tau1* h, const double* drho, const double* ux
 
 /* Copies the current state out as doubles (nx*ny*nz each, host or device per
  * on_device). Any pointer may be NULL to skip that field. Host copies
- * synchronise the handle's stream. Requires set_geometry (LBM_ESTATE). */
+ * synchronise the handle's stream. Host arrays in page-locked memory that
+ * the GPU can address (all four given, dense layout) are written directly
+ * by the export kernel; other host arrays go through a device staging copy.
+ * Requires set_geometry (LBM_ESTATE). */
 lbm_status lbm_tau1_get_fields(lbm_tau1* h, double* drho, double* ux, double* uy,
                                double* uz, int on_device);
 

@@ -493,6 +493,32 @@ lbm_status lbm_tau1_get_fields(lbm_tau1* h, double* drho, double* ux, double* uy
     if (lbm_status st = bgk_refresh_state(h)) return st;
     if (lbm_status st = download_scales(h)) return st;
     const size_t bytes = (size_t)h->n * sizeof(double);
+    if (!on_device && !h->sparse) {
+        // page-locked host arrays that the GPU can address: the export kernel
+        // writes them directly, with no device staging copy
+        double* view[4];
+        bool direct = true;
+        for (int f = 0; f < 4 && direct; ++f) {
+            cudaPointerAttributes at;
+            view[f] = nullptr;
+            if (!dst[f] || cudaPointerGetAttributes(&at, dst[f]) != cudaSuccess) {
+                cudaGetLastError();
+                direct = false;
+            } else if (at.type == cudaMemoryTypeHost && at.devicePointer) {
+                view[f] = static_cast<double*>(at.devicePointer);
+            } else {
+                direct = false;
+            }
+        }
+        if (direct) {
+            cudaError_t e = launch_export_state(h->cfg.storage, h->n, h->buf[h->cur], view, h->flags, h->inv_scale,
+                                                h->stream);
+            ++h->launches;
+            if (e != cudaSuccess) return cuda_fail(h, e, "get_fields: export kernel");
+            LBM_CUDA(h, cudaStreamSynchronize(h->stream), "get_fields: sync");
+            return LBM_OK;
+        }
+    }
     double* tmp = nullptr;
     LBM_CUDA(h, cudaMallocAsync((void**)&tmp, 4 * bytes, h->stream), "get_fields: staging allocation");
     double* ddst[4];
