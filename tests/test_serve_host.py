@@ -248,3 +248,25 @@ def test_live_work_cap():
     res = srv.run(reqs, geometry_fn=fake_geometry, workers=0)
     assert len(res) == 30 and peak[0] <= cap
     assert fb.admit_order == list(range(30))
+
+
+def test_batch_bench_serving_mix_respects_the_cap():
+    """The batched-throughput tool's serving mix follows the request stream
+    in order, skipping requests that would exceed the live-node cap."""
+    from paper_2312_14742_gb300 import batch_bench
+
+    cap = 2 * 64 ** 3
+    masks = batch_bench.serving_mix(20236222, cap_nodes=cap, max_boxes=6)
+    assert 0 < len(masks) <= 6
+    assert sum(m.size for m in masks) <= cap
+    edges = [m.shape[0] for m in masks]
+    expected, tot = [], 0
+    for r in serve.make_requests(400, 20236222):
+        if tot + r.edge ** 3 > cap:
+            continue
+        expected.append(r.edge)
+        tot += r.edge ** 3
+        if len(expected) == 6:
+            break
+    assert edges == expected
+    assert all(m.dtype == np.uint8 and m.shape == (e, e, e) for m, e in zip(masks, edges))
