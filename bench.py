@@ -142,8 +142,9 @@ def bytes_per_fluid_node(storage: str) -> int:
     return 2 * 4 * s
 
 
-TILED_KERNEL_SOURCES = ("tau1_tiled.cu", "tau1_tiled_tma.cu", "tile_column.cuh", "tma.cuh", "tau1_node.cuh",
-                        "pack2.cuh", "common.cuh", "lattice.cuh", "static_for.cuh", "kernels.h")
+TILED_KERNEL_SOURCES = ("tau1_tiled.cu", "tau1_tiled_tma.cu", "tau1_rowpair.cu", "rowpair.cuh", "tile_column.cuh",
+                        "tma.cuh", "tau1_node.cuh", "pack2.cuh", "common.cuh", "lattice.cuh", "static_for.cuh",
+                        "kernels.h")
 
 
 def kernel_source_hash() -> str:

@@ -42,6 +42,7 @@ struct lbm_tau1 {
     int* pos = nullptr;         // sparse: box node of each list entry
     int* nbr = nullptr;         // sparse: neighbour table [(q-1)][nf]
     int64_t launches = 0;
+    unsigned int* dtimeouts = nullptr;  // device counter of staged-copy waits that ran out
     std::string err;
 };
 
@@ -86,6 +87,19 @@ void free_all(lbm_tau1* h)
     if (h->red_host) cudaFreeHost(h->red_host);
     if (h->dscale) cudaFree(h->dscale);
     if (h->rescale_scratch) cudaFree(h->rescale_scratch);
+    if (h->dtimeouts) cudaFree(h->dtimeouts);
+}
+
+// Staged-copy waits that ran out since the last call (reads the device
+// counter on the handle's stream, then clears it).
+unsigned int take_timeouts(lbm_tau1* h)
+{
+    unsigned int v = 0;
+    if (!h->dtimeouts) return 0;
+    if (cudaMemcpyAsync(&v, h->dtimeouts, sizeof(v), cudaMemcpyDefault, h->stream) != cudaSuccess) return 0;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return 0;
+    if (v) cudaMemsetAsync(h->dtimeouts, 0, sizeof(v), h->stream);
+    return v;
 }
 
 lbm_status check_ptr(lbm_tau1* h, const void* p, int on_device, const char* name)
@@ -113,6 +127,7 @@ void fill_args(const lbm_tau1* h, StepArgs& a)
     a.post = h->buf[h->cur ^ 1];
     a.dscale = h->dscale;
     a.seed = (uint32_t)(h->step + 1) * 0x9E3779B9u;
+    a.timeouts = h->dtimeouts;
     for (int f = 0; f < 4; ++f) {
         a.inv_scale[f] = h->inv_scale[f];
         a.scale[f] = h->scale[f];
@@ -370,6 +385,8 @@ lbm_status lbm_tau1_create(const lbm_tau1_config* cfg, lbm_tau1** out)
     if (e == cudaSuccess) e = cudaMalloc(&h->red_partials, (size_t)reduce_blocks(n) * RED_FIELDS * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&h->red_out, RED_FIELDS * sizeof(double));
     if (e == cudaSuccess) e = cudaMallocHost(&h->red_host, RED_FIELDS * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->dtimeouts, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->dtimeouts, 0, sizeof(unsigned int), h->stream);
     if (e == cudaSuccess && sixteen(h)) e = cudaMalloc(&h->dscale, 8 * sizeof(float));
     if (e == cudaSuccess && sixteen(h))
         e = cudaMalloc(&h->rescale_scratch, (size_t)rescale_scratch_floats(n) * sizeof(float));
@@ -395,7 +412,7 @@ lbm_status lbm_tau1_synchronize(lbm_tau1* h)
 {
     if (!h) return fail(nullptr, LBM_EINVAL, "synchronize: NULL handle");
     LBM_CUDA(h, cudaStreamSynchronize(h->stream), "synchronize");
-    if (unsigned t = tma_timeouts_take())
+    if (unsigned t = take_timeouts(h))
         return fail(h, LBM_ETIMEOUT, "synchronize: " + std::to_string(t) + " staged-copy waits ran out");
     return LBM_OK;
 }
@@ -640,7 +657,7 @@ lbm_status lbm_tau1_reduce(lbm_tau1* h, lbm_tau1_stats* out)
     LBM_CUDA(h, cudaMemcpyAsync(h->red_host, h->red_out, RED_FIELDS * sizeof(double), cudaMemcpyDefault,
                                 h->stream), "reduce: copy");
     LBM_CUDA(h, cudaStreamSynchronize(h->stream), "reduce: sync");
-    if (unsigned t = tma_timeouts_take())
+    if (unsigned t = take_timeouts(h))
         return fail(h, LBM_ETIMEOUT, "reduce: " + std::to_string(t) + " staged-copy waits ran out");
     const lbm_status st = fill_stats(h->red_host, h->n, h->cfg.g, h->step, out);
     h->n_fluid = out->n_fluid;

@@ -71,6 +71,7 @@ struct lbm_tau1_batch {
     double* red_partials = nullptr;
     double* red_out = nullptr;   // device [capacity][RED_FIELDS]
     double* red_host = nullptr;  // pinned copy
+    unsigned int* dtimeouts = nullptr;  // device counter of staged-copy waits that ran out
     int nlive = 0;
     int64_t launches = 0;
     std::string err;
@@ -83,6 +84,17 @@ lbm_status bfail(lbm_tau1_batch* b, lbm_status st, const std::string& msg)
     if (b) b->err = msg;
     else set_create_error(msg);
     return st;
+}
+
+// Staged-copy waits that ran out since the last call (the caller has
+// synchronised the batch's stream); clears the counter.
+unsigned int take_timeouts(lbm_tau1_batch* b)
+{
+    unsigned int v = 0;
+    if (!b->dtimeouts) return 0;
+    if (cudaMemcpy(&v, b->dtimeouts, sizeof(v), cudaMemcpyDefault) != cudaSuccess) return 0;
+    if (v) cudaMemset(b->dtimeouts, 0, sizeof(v));
+    return v;
 }
 
 lbm_status bcuda(lbm_tau1_batch* b, cudaError_t e, const char* what)
@@ -273,6 +285,7 @@ void free_batch(lbm_tau1_batch* b)
     if (b->red_partials) cudaFree(b->red_partials);
     if (b->red_out) cudaFree(b->red_out);
     if (b->red_host) cudaFreeHost(b->red_host);
+    if (b->dtimeouts) cudaFree(b->dtimeouts);
     if (b->side_done) cudaEventDestroy(b->side_done);
     if (b->side) cudaStreamDestroy(b->side);
     if (b->capture) cudaStreamDestroy(b->capture);
@@ -345,6 +358,8 @@ lbm_status lbm_tau1_batch_create(const lbm_tau1_batch_config* cfg, lbm_tau1_batc
     if (e == cudaSuccess) e = cudaMalloc(&b->dmaps, (size_t)cap * 2 * sizeof(CUtensorMap));
     if (e == cudaSuccess) e = cudaMalloc(&b->red_partials, (size_t)1024 * RED_FIELDS * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&b->red_out, (size_t)cap * RED_FIELDS * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->dtimeouts, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->dtimeouts, 0, sizeof(unsigned int), b->stream);
     if (e == cudaSuccess) e = cudaMallocHost(&b->red_host, (size_t)cap * RED_FIELDS * sizeof(double));
     if (e == cudaSuccess && cfg->hbm_budget == 0) {
         size_t fr = 0, tot = 0;
@@ -432,6 +447,7 @@ lbm_status lbm_tau1_batch_admit(lbm_tau1_batch* b, const lbm_tau1_config* cfg, c
     rec.a.nx = cfg->nx;
     rec.a.ny = cfg->ny;
     rec.a.nz = cfg->nz;
+    rec.a.timeouts = b->dtimeouts;
     for (int d = 0; d < 3; ++d) {
         rec.a.periodic[d] = per[d];
         rec.a.g[d] = cfg->g[d];
@@ -544,6 +560,8 @@ lbm_status lbm_tau1_batch_stats(lbm_tau1_batch* b, int32_t n, const int32_t* slo
     BCUDA(b, cudaMemcpyAsync(b->red_host, b->red_out, (size_t)n * RED_FIELDS * sizeof(double), cudaMemcpyDefault,
                              b->stream), "batch_stats: copy");
     BCUDA(b, cudaStreamSynchronize(b->stream), "batch_stats: sync");
+    if (unsigned t = take_timeouts(b))
+        return bfail(b, LBM_ETIMEOUT, "batch_stats: " + std::to_string(t) + " staged-copy waits ran out");
     lbm_status worst = LBM_OK;
     for (int i = 0; i < n; ++i) {
         const Slot& s = b->slots[slots[i]];
@@ -585,6 +603,8 @@ lbm_status lbm_tau1_batch_synchronize(lbm_tau1_batch* b)
 {
     if (!b) return bfail(nullptr, LBM_EINVAL, "batch_synchronize: NULL batch");
     BCUDA(b, cudaStreamSynchronize(b->stream), "batch_synchronize");
+    if (unsigned t = take_timeouts(b))
+        return bfail(b, LBM_ETIMEOUT, "batch_synchronize: " + std::to_string(t) + " staged-copy waits ran out");
     return LBM_OK;
 }
 

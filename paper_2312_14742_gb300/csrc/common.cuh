@@ -199,6 +199,7 @@ struct StepArgs {
     float scale[4];
     const float* dscale; // 16-bit storage: device float[8] = {S_f, 1/S_f}; stored = value * S_f
     uint32_t seed;       // stochastic-rounding seed of this step
+    unsigned int* timeouts;  // device counter of staged-copy waits that ran out (staged kernels)
 };
 
 // Scales of the 16-bit formats, read once per thread from device memory.

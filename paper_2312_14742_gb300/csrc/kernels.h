@@ -13,7 +13,7 @@ namespace lbm {
 cudaError_t launch_tau1_simple(int q, int storage, const StepArgs& a, cudaStream_t s);
 cudaError_t launch_tau1_tiled(int q, int storage, int variant, const StepArgs& a, cudaStream_t s);
 bool tau1_tiled_supported(int q, int storage, int64_t n);
-int tau1_tiled_variants(int q, int storage);  // tile shapes x z-chunk heights
+int tau1_tiled_variants(int q, int storage);  // (row-pair + pair-position tile shapes) x z-chunk heights
 int tau1_tile_shapes(int storage);            // tile shapes (the batched kernel's variants)
 // Staged (TMA) form of the tiled kernel: same bits; for boxes with full tiles.
 bool tau1_tiled_tma_ok(int q, int storage, int variant, const StepArgs& a);
@@ -21,8 +21,11 @@ cudaError_t launch_tau1_tiled_tma(int q, int storage, int variant, const StepArg
 // Tensor map of a state copy for the staged kernels: 3D {4 nx, ny, nz} values,
 // box {4 (32 + 2 XOFF), box_rows, 1}.
 cudaError_t encode_state_map(int storage, const void* base, int nx, int ny, int nz, int box_rows, CUtensorMap* map);
-// Waits of the staged kernel that ran out (counted on the device since the last call), then reset.
-unsigned int tma_timeouts_take();
+// Row-pair form (shuffle exchange within rows, shared memory across warp
+// seams): same bits; for boxes with full tiles of its shape.
+int tau1_rowpair_shapes(int storage);
+bool tau1_rowpair_ok(int q, int storage, int shape, const StepArgs& a);
+cudaError_t launch_tau1_rowpair(int q, int storage, int shape, int zchunk, const StepArgs& a, cudaStream_t s);
 
 // Sparse layout (fluid list + neighbour table). count: counts[0..nb) become
 // the exclusive prefix sums of the fluid counts of the scan blocks and

@@ -31,12 +31,9 @@ cudaError_t launch_t(const StepArgs& a, int zchunk, cudaStream_t s)
     constexpr int H = Shape<Q, E, V>::H;
     using C = TCfg<Q, 32, H, E>;
     auto kern = tau1_tiled_kernel<Q, ST, H, Shape<Q, E, V>::MINB>;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    // the attribute is per device; setting it on every launch is cheap
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    if (e != cudaSuccess) return e;
     const int ntx = (a.nx + 31) / 32;
     const int nty = (a.ny + 2 * H - 1) / (2 * H);
     const int ntiles = ntx * nty;
@@ -73,12 +70,27 @@ bool tau1_tiled_supported(int q, int storage, int64_t n)
     return (q == 19 || q == 27) && storage >= ST_F64 && storage <= ST_BF16S && n > 0 && n < ((int64_t)1 << 31);
 }
 
-int tau1_tiled_variants(int, int storage) { return 2 * tile_shapes(storage); }
+// Variants of a single box: [0, 2R) the row-pair kernel (R tile shapes, then
+// 24- or 32-plane chunks), [2R, 2R + 2T) the pair-position kernel (T shapes,
+// same chunk rule; staged when the tiles are full). A row-pair variant that
+// does not fit the box (ragged tiles) runs the pair-position variant with the
+// same chunk height instead.
+int tau1_tiled_variants(int, int storage) { return 2 * tau1_rowpair_shapes(storage) + 2 * tile_shapes(storage); }
 
 int tau1_tile_shapes(int storage) { return tile_shapes(storage); }
 
 cudaError_t launch_tau1_tiled(int q, int storage, int variant, const StepArgs& a, cudaStream_t s)
 {
+    const int nr = tau1_rowpair_shapes(storage);
+    if (variant < 0 || variant >= tau1_tiled_variants(q, storage)) return cudaErrorInvalidValue;
+    if (variant < 2 * nr) {
+        const int shape = variant % nr;
+        if (tau1_rowpair_ok(q, storage, shape, a))
+            return launch_tau1_rowpair(q, storage, shape, variant < nr ? 24 : 32, a, s);
+        variant = variant < nr ? 0 : tile_shapes(storage);
+    } else {
+        variant -= 2 * nr;
+    }
     if (tau1_tiled_tma_ok(q, storage, variant, a)) return launch_tau1_tiled_tma(q, storage, variant, a, s);
     switch (q * 10 + storage) {
     case 190 + ST_F64: return launch_v<19, ST_F64>(variant, a, s);

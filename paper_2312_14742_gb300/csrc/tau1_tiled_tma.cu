@@ -92,14 +92,11 @@ cudaError_t launch_t(const StepArgs& a, int zchunk, cudaStream_t s)
     constexpr size_t SMEM = tile_smem<Q, ST, H, true>();
     static_assert(SMEM <= 227 * 1024, "shared memory of one block");
     auto kern = tau1_tiled_tma_kernel<Q, ST, H, Shape<Q, E, V>::MINB>;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    // the attribute is per device; setting it on every launch is cheap
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
+    if (e != cudaSuccess) return e;
     CUtensorMap map;
-    cudaError_t e = encode_state<ST>(&map, a, 2 * H + 2);
+    e = encode_state<ST>(&map, a, 2 * H + 2);
     if (e != cudaSuccess) return e;
     const int ntx = (a.nx + 31) / 32;
     const int ntiles = ntx * ((a.ny + 2 * H - 1) / (2 * H));
@@ -165,14 +162,6 @@ cudaError_t encode_state_map(int storage, const void* base, int nx, int ny, int 
     case ST_BF16S: return encode_at<ST_BF16S>(map, base, nx, ny, nz, box_rows);
     default: return cudaErrorInvalidValue;
     }
-}
-
-unsigned int tma_timeouts_take()
-{
-    unsigned int v = 0, zero = 0;
-    if (cudaMemcpyFromSymbol(&v, g_tma_timeouts, sizeof(v)) != cudaSuccess) return 0;
-    if (v) cudaMemcpyToSymbol(g_tma_timeouts, &zero, sizeof(zero));
-    return v;
 }
 
 }  // namespace lbm

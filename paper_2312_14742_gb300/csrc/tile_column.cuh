@@ -213,9 +213,11 @@ __device__ __forceinline__ void track_amax(float (&m)[4], E d, E ux, E uy, E uz)
 // AMAX, amax[f] collects the largest |value| of field f among the nodes this
 // thread stores. With TMA the raw records come from shared-memory stages
 // (initialised by stage_init; *phase_io carries their phase bits from call
-// to call) filled by the tensor unit through tmap (the state read, viewed as a 3D
-// array of 4 nx x ny x nz values); the tile must lie inside the box, and halo
-// nodes outside it are read from global memory (periodic images) or are walls.
+// to call) filled by the tensor unit through tmap (the state read, viewed as a
+// 3D array of 4 nx x ny x nz values); the tile must lie inside the box, and
+// halo nodes outside it are read from global memory (periodic images) or are
+// walls. A wait that runs out is counted in *a.timeouts, and the thread then
+// tries no later wait and stores nothing more in this call.
 template <int Q, int ST, int H, bool AMAX, bool TMA = false>
 __device__ __forceinline__ void tile_column(const StepArgs& a, const Scales& sc, int x0, int y0, int z0, int z1,
                                             unsigned char* smem_raw, float (&amax)[4],
@@ -311,7 +313,7 @@ __device__ __forceinline__ void tile_column(const StepArgs& a, const Scales& sc,
     // thread 0 starts the copy of plane p's box into its stage
     [[maybe_unused]] auto issue = [&](int p) {
         int gz = p;
-        if (tid == 0 && wrap_coord(gz, a.nz, a.periodic[2])) {
+        if (tid == 0 && !timed_out && wrap_coord(gz, a.nz, a.periodic[2])) {
             const int st = (p - z0 + 1) % SC::NSTAGE;
             mbar_arrive_expect_tx(&mbar[st], SC::BOX_BYTES);
             tma_load_3d(stages + st * SC::STAGE_BYTES, tmap, &mbar[st], 4 * (x0 - SC::XOFF), y0 - 1, gz);
@@ -331,8 +333,11 @@ __device__ __forceinline__ void tile_column(const StepArgs& a, const Scales& sc,
             return;
         }
         const int st = (p - z0 + 1) % SC::NSTAGE;
-        if (!mbar_wait_bounded(&mbar[st], (phase >> st) & 1u)) timed_out = true;
-        phase ^= 1u << st;
+        // after a wait ran out, no later wait is tried and nothing more is stored
+        if (!timed_out) {
+            if (!mbar_wait_bounded(&mbar[st], (phase >> st) & 1u)) timed_out = true;
+            phase ^= 1u << st;
+        }
         const unsigned char* base = stages + st * SC::STAGE_BYTES;
         auto cell = [&](int c, int r) { return base + (size_t)(r * SC::SW + c) * SC::REC; };
         S::load_at(cell(tx + SC::XOFF, ty + 1), sc.inv, r_own.d.v.x, r_own.ux.v.x, r_own.uy.v.x, r_own.uz.v.x);
@@ -555,12 +560,12 @@ __device__ __forceinline__ void tile_column(const StepArgs& a, const Scales& sc,
         L d_, x_, y_, z_;
         node_finish<Q, L>(acc, d_, x_, y_, z_);
         const uint32_t zoff = (uint32_t)(p - 1) * nxy;
-        if (fluidA_prev) {
+        if (fluidA_prev && !timed_out) {
             step_store<ST>(a.post, zoff + (uint32_t)gx + (uint32_t)a.nx * (uint32_t)gyA, d_.v.x, x_.v.x, y_.v.x,
                            z_.v.x, sc.s, a.seed);
             if constexpr (AMAX) track_amax(amax, d_.v.x, x_.v.x, y_.v.x, z_.v.x);
         }
-        if (fluidB_prev) {
+        if (fluidB_prev && !timed_out) {
             step_store<ST>(a.post, zoff + (uint32_t)gx + (uint32_t)a.nx * (uint32_t)gyB, d_.v.y, x_.v.y, y_.v.y,
                            z_.v.y, sc.s, a.seed);
             if constexpr (AMAX) track_amax(amax, d_.v.y, x_.v.y, y_.v.y, z_.v.y);
@@ -632,7 +637,7 @@ __device__ __forceinline__ void tile_column(const StepArgs& a, const Scales& sc,
         finish_prev(z1, f01, fsg);
     }
     if constexpr (TMA) {
-        if (timed_out) atomicAdd(&g_tma_timeouts, 1u);
+        if (timed_out && a.timeouts) atomicAdd(a.timeouts, 1u);
         *phase_io = phase;
     }
 }

@@ -14,10 +14,6 @@
 
 namespace lbm {
 
-// one per translation unit (no relocatable device code); the staged kernel's
-// unit reports its own
-static __device__ unsigned int g_tma_timeouts = 0;
-
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
