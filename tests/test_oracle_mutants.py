@@ -32,6 +32,9 @@ MUTANTS = {
     "transposed index": ("(size_t)x + (size_t)G->nx * ((size_t)y + (size_t)G->ny * (size_t)z)",
                          "(size_t)y + (size_t)G->ny * ((size_t)x + (size_t)G->nx * (size_t)z)"),
     "wall counted as fluid": ("if (!G->periodic[a]) return 1;", "if (!G->periodic[a]) p[a] = 0;"),
+    "reduction without the half-step force": ("double px = ux[i] + 0.5 * g[0]", "double px = ux[i] + 0.0 * g[0]"),
+    "superficial mean over fluid nodes": ("out[2] = sx / (double)n;", "out[2] = sx / nf;"),
+    "mass over all nodes": ("if (solid[i]) continue;\n        nf += 1.0;", "nf += solid[i] ? 0.0 : 1.0;"),
 }
 
 
@@ -77,6 +80,19 @@ def battery(lib):
     o = oracle.Domain(19, solid, periodic=(1, 0, 1), g=gb, lib=lib).tau1_run(st, 2)
     if any(np.max(np.abs(o[a] - ref[a])) > 1e-14 for a in range(4)):
         failed.append("brute")
+    # reduction of isolated nodes after one step (closed forms: -u - g/2, sum of 1 + drho)
+    solid = np.ones((4, 4, 4), np.uint8)
+    solid[::2, ::2, ::2] = 0
+    fl = solid == 0
+    st = lbm_inputs.random_fields(solid.shape, 35, 1e-2, 2e-2, solid)
+    gr = np.array([3e-5, -1e-5, 2e-5])
+    D = oracle.Domain(19, solid, g=gr, lib=lib)
+    r = D.reduce(D.tau1_step(st))
+    phys = -st[1][fl] - 0.5 * gr[0]
+    if (abs(r["mass"] - math.fsum(1.0 + st[0][fl])) > 1e-13
+            or abs(r["mean_ux_superficial"] - math.fsum(phys) / solid.size) > 1e-15
+            or abs(r["mean_u_fluid"][0] - math.fsum(phys) / fl.sum()) > 1e-15):
+        failed.append("reduce")
     return failed
 
 

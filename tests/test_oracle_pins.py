@@ -373,6 +373,61 @@ def test_nodes_matches_full_step():
             assert got[m, a] == full[a].reshape(-1)[i]
 
 
+@pytest.mark.parametrize("q", LATTICES)
+def test_reduce_uniform_acceleration_closed_form(q):
+    """A periodic box with no walls under a body force: rho stays rho0 and u
+    gains exactly g per step (sum c f^eq(v) = rho v), so after t steps the
+    reduction of the state has closed forms: mass N (1 + drho0), physical
+    velocity u0 + (t + 1/2) g at every node (velocity shift, Algorithm
+    'Optimized Tau1 ... stores velocity' with reading c5), hence the mean,
+    the maximum |u| and the Darcy permeability nu (u0_x + (t + 1/2) g_x) / g_x."""
+    shape = (5, 4, 6)
+    n = int(np.prod(shape))
+    solid = np.zeros(shape, np.uint8)
+    d0, u0 = 3e-3, np.array([1e-3, -2e-3, 5e-4])
+    g = np.array([1e-5, 2e-6, -4e-6])
+    t = 7
+    st = (np.full(shape, d0), np.full(shape, u0[0]), np.full(shape, u0[1]), np.full(shape, u0[2]))
+    D = oracle.Domain(q, solid, g=g)
+    r = D.reduce(D.tau1_run(st, t))
+    phys = u0 + (t + 0.5) * g
+    assert r["n_fluid"] == n
+    assert r["mass"] == pytest.approx(n * (1.0 + d0), rel=1e-14)
+    for a in range(3):
+        assert abs(r["mean_u_fluid"][a] - phys[a]) < 1e-15
+    assert abs(r["mean_ux_superficial"] - phys[0]) < 1e-15
+    assert r["max_abs_u"] == pytest.approx(float(np.linalg.norm(phys)), rel=1e-12)
+    assert r["permeability"] == pytest.approx((1.0 / 6.0) * phys[0] / g[0], rel=1e-10)
+
+
+@pytest.mark.parametrize("q", LATTICES)
+def test_reduce_isolated_nodes_closed_form(q):
+    """Fluid only where x, y and z are all even: every fluid node is isolated
+    (its 18 or 26 neighbours are solid), so one step gives rho' = rho and
+    u' = -(u + g) exactly (Algorithm 'Complete Tau1 ... halfway
+    bounce-back'). The reduction then has closed forms in the initial
+    per-node state: mass sum(1 + drho), physical velocity -(u + g) + g/2 =
+    -u - g/2, its mean over the fluid nodes, its superficial mean over all N
+    nodes (an eighth of the fluid mean here) and its largest magnitude."""
+    nx, ny, nz = 6, 4, 8
+    solid = np.ones((nz, ny, nx), np.uint8)
+    solid[::2, ::2, ::2] = 0
+    fl = solid == 0
+    st = lbm_inputs.random_fields(solid.shape, 4711, 1e-2, 2e-2, solid)
+    g = np.array([3e-5, -1e-5, 2e-5])
+    D = oracle.Domain(q, solid, g=g)
+    r = D.reduce(D.tau1_step(st))
+    nf = int(fl.sum())
+    phys = [-st[1 + a][fl] - 0.5 * g[a] for a in range(3)]
+    assert nf == nx * ny * nz // 8 and r["n_fluid"] == nf
+    assert r["mass"] == pytest.approx(math.fsum(1.0 + st[0][fl]), rel=1e-15)
+    for a in range(3):
+        assert r["mean_u_fluid"][a] == pytest.approx(math.fsum(phys[a]) / nf, rel=1e-12, abs=1e-18)
+    assert r["mean_ux_superficial"] == pytest.approx(math.fsum(phys[0]) / solid.size, rel=1e-12, abs=1e-18)
+    mags = np.sqrt(phys[0] ** 2 + phys[1] ** 2 + phys[2] ** 2)
+    assert r["max_abs_u"] == pytest.approx(float(mags.max()), rel=1e-14)
+
+
 def test_reduce_definitions():
     solid = lbm_inputs.random_mask(5, 4, 3, 0.3, 21)
     st = lbm_inputs.random_fields(solid.shape, 22, 1e-3, 1e-3, solid)
