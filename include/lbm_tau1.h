@@ -293,7 +293,8 @@ const char* lbm_tau1_batch_last_error(const lbm_tau1_batch* b); /* never NULL */
  * overlaps on the GPU (streams with no ordering between them) race on it.
  * The first call on a device looks up the array's device address (with that
  * device current) and caches it; make that first call before any stream
- * capture.
+ * capture. The cached address does not survive cudaDeviceReset of that
+ * device: do not call this entry point on a device after resetting it.
  *
  * Arguments: storage (lbm_storage) and n = number of nodes; drho, ux, uy, uz
  * = device arrays of n values in that storage format; inv_scale = host array

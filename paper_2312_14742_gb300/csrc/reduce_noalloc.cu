@@ -48,7 +48,10 @@ lbm_status noalloc_fail(lbm_status st, const char* what, cudaError_t e = cudaSuc
 
 // Looks up, once per device and with that device current, the device address
 // of the scratch array. In host code the name g_noalloc_partials is only a
-// host-side stand-in, never a device address.
+// host-side stand-in, never a device address. The cached address belongs to
+// the device's primary context: it does not survive cudaDeviceReset (the
+// module, and with it the array, is loaded anew), so a process that resets a
+// device must not call this entry point on that device afterwards.
 lbm_status scratch_address(void** out)
 {
     int dev = -1;
@@ -81,6 +84,8 @@ lbm_status lbm_tau1_reduce_noalloc(int32_t storage, int64_t n, const void* drho,
     if (n < 1) return noalloc_fail(LBM_EINVAL, "n must be >= 1");
     if (n > LBM_TAU1_NOALLOC_MAX_NODES) return noalloc_fail(LBM_EINVAL, "n exceeds LBM_TAU1_NOALLOC_MAX_NODES");
     if (!drho || !ux || !uy || !uz || !solid || !g || !out) return noalloc_fail(LBM_EINVAL, "NULL argument");
+    // reduce_blocks() never asks for more than LBM_TAU1_NOALLOC_MAX_BLOCKS rows
+    // (it caps the block count); the check guards the array against a change there
     const int blocks = reduce_blocks(n);
     if (blocks > LBM_TAU1_NOALLOC_MAX_BLOCKS)
         return noalloc_fail(LBM_EINVAL, "n needs more partial rows than the static scratch holds");

@@ -79,6 +79,55 @@ def test_noalloc_matches_reduce_on_consecutive_calls():
             _check(raw, ref, solid.size)
 
 
+def test_noalloc_16bit_with_scales_matches_oracle():
+    """16-bit storage with non-unit per-field scales (value = stored *
+    inv_scale): the noalloc reduction of the stored arrays equals the FP64
+    oracle's reduction of the dequantised state (exact in FP64, since the
+    scales are powers of two), on two calls in a row for each format."""
+    torch = pytest.importorskip("torch")
+    import oracle
+    assert torch.cuda.is_available()
+    build.build()
+    lbm.load()
+    dev = torch.device("cuda", 0)
+    g = (2e-5, -1e-5, 3e-6)
+    dims = (40, 36, 30)
+    solid, st = _state(dims, 303)
+    ref_dom = oracle.Domain(19, solid, g=g)
+    for storage, np16, scale in (("f16s", np.float16, (2.0 ** 10, 2.0 ** 12, 2.0 ** 11, 2.0 ** 13)),
+                                 ("bf16s", None, (2.0 ** 4, 2.0 ** -2, 2.0 ** 6, 2.0 ** 3))):
+        if np16 is not None:
+            stored = [np.ascontiguousarray((a * s).astype(np16)) for a, s in zip(st, scale)]
+            deq = [b.astype(np.float64) / s for b, s in zip(stored, scale)]
+            tens = [torch.from_numpy(b.view(np.int16)) for b in stored]
+        else:
+            # BF16: round the FP32 value to the nearest bfloat16 with torch, on the CPU
+            tb = [torch.from_numpy(a * s).to(torch.float32).to(torch.bfloat16) for a, s in zip(st, scale)]
+            deq = [b.to(torch.float64).numpy() / s for b, s in zip(tb, scale)]
+            tens = [b.view(torch.int16) for b in tb]
+        fields = [t.contiguous().to(dev) for t in tens]
+        mask = torch.from_numpy(np.ascontiguousarray(solid)).to(dev)
+        inv = (ctypes.c_float * 4)(*[1.0 / s for s in scale])
+        gg = (ctypes.c_double * 3)(*g)
+        ref = ref_dom.reduce(deq)
+        nf = ref["n_fluid"]
+        for _ in range(2):
+            out = torch.full((8,), float("nan"), dtype=torch.float64, device=dev)
+            rc = lbm.lbm_tau1_reduce_noalloc(lbm.STORAGE[storage], solid.size, *[f.data_ptr() for f in fields], inv,
+                                             mask.data_ptr(), gg, out.data_ptr(),
+                                             torch.cuda.current_stream(dev).cuda_stream)
+            assert rc == lbm.LBM_OK, lbm.lbm_tau1_noalloc_last_error()
+            torch.cuda.synchronize(dev)
+            raw = out.cpu().numpy()
+            assert int(raw[0]) == nf and int(raw[6]) == 0
+            assert abs(raw[1] - (ref["mass"] - nf)) <= 1e-12 * max(1.0, abs(ref["mass"] - nf))
+            assert abs(raw[2] / solid.size - ref["mean_ux_superficial"]) <= 1e-12 * abs(ref["mean_ux_superficial"])
+            for a in range(3):
+                want = ref["mean_u_fluid"][a]
+                assert abs(raw[2 + a] / nf - want) <= 1e-12 * abs(want), (storage, a)
+            assert abs(raw[5] - ref["max_abs_u"]) <= 1e-12 * ref["max_abs_u"]
+
+
 def test_noalloc_rejects_bad_sizes():
     build.build()
     lbm.load()
