@@ -21,6 +21,7 @@ struct lbm_tau1 {
     void* buf[2] = {};          // ping-pong copies of the state records
     int cur = 0;                // buf[cur] is the current (pre) state
     void* fbuf[2] = {};         // BGK scheme: ping-pong populations [q][n]
+    uint32_t* bgk_mask = nullptr;  // BGK scheme: wall links of every node
     int fcur = 0;
     bool bgk = false;
     uint8_t* flags = nullptr;   // node flags
@@ -79,6 +80,7 @@ void free_all(lbm_tau1* h)
         if (h->buf[b]) cudaFree(h->buf[b]);
         if (h->fbuf[b]) cudaFree(h->fbuf[b]);
     }
+    if (h->bgk_mask) cudaFree(h->bgk_mask);
     if (h->flags) cudaFree(h->flags);
     if (h->pos) cudaFree(h->pos);
     if (h->nbr) cudaFree(h->nbr);
@@ -195,18 +197,24 @@ lbm_status bgk_refresh_state(lbm_tau1* h)
     if (!h->bgk || h->step == 0) return LBM_OK;
     StepArgs a;
     fill_args(h, a);
-    cudaError_t e = launch_bgk_moments(h->cfg.q, h->cfg.storage, a, h->fbuf[h->fcur ^ 1], h->buf[h->cur], h->stream);
+    cudaError_t e = launch_bgk_moments(h->cfg.q, h->cfg.storage, a, h->fbuf[h->fcur ^ 1], h->buf[h->cur],
+                                       h->bgk_mask, h->stream);
     ++h->launches;
     if (e != cudaSuccess) return cuda_fail(h, e, "bgk moments kernel");
     return LBM_OK;
 }
 
-// BGK: populations from the current state records.
+// BGK: wall links from the node flags, populations from the current state records.
 lbm_status bgk_from_state(lbm_tau1* h)
 {
     if (!h->bgk) return LBM_OK;
     StepArgs a;
     fill_args(h, a);
+    {
+        cudaError_t e = launch_bgk_mask(h->cfg.q, a, h->flags, h->bgk_mask, h->stream);
+        ++h->launches;
+        if (e != cudaSuccess) return cuda_fail(h, e, "bgk wall-link kernel");
+    }
     // both copies: the step kernel writes fluid nodes only, so the solid
     // nodes of the other copy must already hold their NaN marker
     for (int b = 0; b < 2; ++b) {
@@ -284,7 +292,8 @@ lbm_status launch_step(lbm_tau1* h)
     StepArgs a;
     fill_args(h, a);
     if (h->bgk) {
-        cudaError_t e = launch_bgk_step(h->cfg.q, h->cfg.storage, a, h->fbuf[h->fcur], h->fbuf[h->fcur ^ 1], h->stream);
+        cudaError_t e = launch_bgk_step(h->cfg.q, h->cfg.storage, a, h->fbuf[h->fcur], h->fbuf[h->fcur ^ 1],
+                                        h->bgk_mask, h->stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "bgk step launch");
         ++h->launches;
         h->fcur ^= 1;
@@ -381,6 +390,7 @@ lbm_status lbm_tau1_create(const lbm_tau1_config* cfg, lbm_tau1** out)
     if (h->bgk)
         for (int b = 0; b < 2 && e == cudaSuccess; ++b)
             e = cudaMalloc(&h->fbuf[b], (size_t)n * cfg->q * (cfg->storage == LBM_F64 ? 8 : 4));
+    if (h->bgk && e == cudaSuccess) e = cudaMalloc((void**)&h->bgk_mask, (size_t)n * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMalloc(&h->flags, (size_t)n);
     if (e == cudaSuccess) e = cudaMalloc(&h->red_partials, (size_t)reduce_blocks(n) * RED_FIELDS * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&h->red_out, RED_FIELDS * sizeof(double));

@@ -42,11 +42,15 @@ cudaError_t launch_export_sparse(int storage, int nf, const void* src, const int
                                  const float inv_scale[4], cudaStream_t s);
 
 // Standard BGK (tau = 1, stored populations) comparison kernels. Populations:
-// [q][n] in the storage type (FP32 or FP64). init: populations from state
-// records; moments: state records from the populations a step would gather.
+// [q][n] in the storage type (FP32 or FP64). mask: one word per node of wall
+// links (built by launch_bgk_mask from the node flags). init: populations from
+// state records; moments: state records from the populations a step would gather.
 bool bgk_supported(int q, int storage);
-cudaError_t launch_bgk_step(int q, int storage, const StepArgs& a, const void* fin, void* fout, cudaStream_t s);
-cudaError_t launch_bgk_moments(int q, int storage, const StepArgs& a, const void* fin, void* state, cudaStream_t s);
+cudaError_t launch_bgk_mask(int q, const StepArgs& a, const uint8_t* flags, uint32_t* mask, cudaStream_t s);
+cudaError_t launch_bgk_step(int q, int storage, const StepArgs& a, const void* fin, void* fout, const uint32_t* mask,
+                            cudaStream_t s);
+cudaError_t launch_bgk_moments(int q, int storage, const StepArgs& a, const void* fin, void* state,
+                               const uint32_t* mask, cudaStream_t s);
 cudaError_t launch_bgk_init(int q, int storage, const StepArgs& a, const void* state, void* fout, cudaStream_t s);
 
 // 16-bit storage scales (device float[8]): re-chosen from the state's maxima
