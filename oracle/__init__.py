@@ -54,6 +54,8 @@ def load(path: str | None = None):
     lib.orc_feq_dev.restype = _D
     lib.orc_tau1_step.argtypes = [_I, _I, _I, _I, _P, _P, _P] + [_P] * 8
     lib.orc_tau1_run.argtypes = [_I, _I, _I, _I, _P, _P, _P] + [_P] * 4 + [_I64]
+    lib.orc_tau1_step_bc.argtypes = [_I, _I, _I, _I, _P, _P, _P, _P] + [_P] * 8
+    lib.orc_tau1_run_bc.argtypes = [_I, _I, _I, _I, _P, _P, _P, _P] + [_P] * 4 + [_I64]
     lib.orc_tau1_nodes.argtypes = [_I, _I, _I, _I, _P, _P, _P] + [_P] * 4 + [_P, _I64, _P]
     lib.orc_bgk_init.argtypes = [_I, _I, _I, _I, _P, _D, _P] + [_P] * 4 + [_P]
     lib.orc_bgk_step.argtypes = [_I, _I, _I, _I, _P, _P, _D, _P, _P, _P] + [_P] * 4
@@ -71,14 +73,18 @@ def _f64(a):
 
 
 class Domain:
-    """Geometry and driving of one box: lattice q, mask (nz,ny,nx), periodicity, g."""
+    """Geometry and driving of one box: lattice q (9 = D2Q9, one plane), mask
+    (nz,ny,nx), periodicity, g, and optional constant-density (Zou-He)
+    faces ``pressure = (axis, rho at coordinate 0, rho at coordinate n-1)``
+    on a non-periodic axis."""
 
-    def __init__(self, q: int, solid: np.ndarray, periodic=(1, 1, 1), g=(0.0, 0.0, 0.0), lib=None):
+    def __init__(self, q: int, solid: np.ndarray, periodic=(1, 1, 1), g=(0.0, 0.0, 0.0), lib=None, pressure=None):
         self.q = int(q)
         self.solid = np.ascontiguousarray(solid, dtype=np.uint8)
         self.nz, self.ny, self.nx = self.solid.shape
         self.periodic = np.asarray(periodic, dtype=np.int32)
         self.g = np.asarray(g, dtype=np.float64)
+        self.bc = np.asarray(pressure if pressure is not None else (-1.0, 1.0, 1.0), dtype=np.float64)
         self.lib = lib or load()
 
     @property
@@ -89,6 +95,10 @@ class Domain:
         return (self.q, self.nx, self.ny, self.nz, self.periodic.ctypes.data, self.g.ctypes.data,
                 self.solid.ctypes.data)
 
+    def _args_bc(self):
+        return (self.q, self.nx, self.ny, self.nz, self.periodic.ctypes.data, self.g.ctypes.data,
+                self.bc.ctypes.data, self.solid.ctypes.data)
+
     def zero_state(self):
         z = np.zeros(self.shape, dtype=np.float64)
         return (z, z.copy(), z.copy(), z.copy())
@@ -96,14 +106,14 @@ class Domain:
     def tau1_step(self, state):
         s = [_f64(a) for a in state]
         o = [np.empty(self.shape, dtype=np.float64) for _ in range(4)]
-        rc = self.lib.orc_tau1_step(*self._args(), *[a.ctypes.data for a in s], *[a.ctypes.data for a in o])
+        rc = self.lib.orc_tau1_step_bc(*self._args_bc(), *[a.ctypes.data for a in s], *[a.ctypes.data for a in o])
         if rc != 0:
             raise ValueError("orc_tau1_step failed")
         return tuple(o)
 
     def tau1_run(self, state, nsteps: int):
         s = [np.array(a, dtype=np.float64, order="C", copy=True) for a in state]
-        rc = self.lib.orc_tau1_run(*self._args(), *[a.ctypes.data for a in s], int(nsteps))
+        rc = self.lib.orc_tau1_run_bc(*self._args_bc(), *[a.ctypes.data for a in s], int(nsteps))
         if rc != 0:
             raise ValueError("orc_tau1_run failed")
         return tuple(s)
@@ -155,7 +165,7 @@ def lattice(q: int, lib=None):
     w = np.empty(q, dtype=np.float64)
     inv = np.empty(q, dtype=np.int32)
     if lib.orc_lattice(q, c.ctypes.data, w.ctypes.data, inv.ctypes.data) != 0:
-        raise ValueError(f"no lattice D3Q{q}")
+        raise ValueError(f"no lattice with q = {q}")
     return c, w, inv
 
 

@@ -26,8 +26,8 @@
  *                    equilibrium, relax, store.
  *
  * Readings fixed here (the paper is silent or ambiguous on these):
- *  - Lattices D3Q19 and D3Q27 with the textbook velocities and weights
- *    (Qian et al. 1992).
+ *  - Lattices D2Q9 (one plane, nz = 1), D3Q19 and D3Q27 with the textbook
+ *    velocities and weights (Qian et al. 1992).
  *  - A bounced link adds c_k * f^eq_{inv k}(own rho*, own u*): the reflected
  *    population travels along c_k.
  *  - Body force: velocity shift. Every equilibrium is evaluated at
@@ -76,19 +76,28 @@ static const int VEL27[27][3] = {
     { 1,-1, 1}, {-1, 1,-1}, {-1, 1, 1}, { 1,-1,-1},
 };
 
+/* D2Q9 (the plane z = const): rest, 4 axis directions, 4 diagonals. */
+static const int VEL9[9][3] = {
+    { 0, 0, 0}, { 1, 0, 0}, {-1, 0, 0}, { 0, 1, 0}, { 0,-1, 0},
+    { 1, 1, 0}, {-1,-1, 0}, { 1,-1, 0}, {-1, 1, 0},
+};
+
 static int lattice_make(int q, lattice* L)
 {
     /* weights by squared speed |c|^2 = 0,1,2,3 */
+    static const double W9[4] = {4.0 / 9.0, 1.0 / 9.0, 1.0 / 36.0, 0.0};
     static const double W19[4] = {1.0 / 3.0, 1.0 / 18.0, 1.0 / 36.0, 0.0};
     static const double W27[4] = {8.0 / 27.0, 2.0 / 27.0, 1.0 / 54.0, 1.0 / 216.0};
     const double* W;
-    if (q == 19) W = W19;
+    const int (*V)[3] = VEL27;
+    if (q == 9) { W = W9; V = VEL9; }
+    else if (q == 19) W = W19;
     else if (q == 27) W = W27;
     else return -1;
     L->q = q;
     for (int k = 0; k < q; ++k) {
         int s = 0;
-        for (int a = 0; a < 3; ++a) { L->c[k][a] = VEL27[k][a]; s += VEL27[k][a] * VEL27[k][a]; }
+        for (int a = 0; a < 3; ++a) { L->c[k][a] = V[k][a]; s += V[k][a] * V[k][a]; }
         L->w[k] = W[s];
     }
     /* opposite direction found by search, not by position */
@@ -165,22 +174,76 @@ static int link_source(const grid* G, const lattice* L, int k, int x, int y, int
  * "Optimized Tau1 that stores velocity": accumulate, over k in order
  * 0..q-1, the equilibrium arriving along c_k, then one reciprocal of rho.
  */
-static void tau1_node(const grid* G, const lattice* L, const double g[3],
+/* The population arriving at (x, y, z) = node i along c_k: the equilibrium
+ * of the source x - c_k, or, for a wall link, halfway bounce-back of the
+ * node's own previous rho*, u* in direction inv(k). */
+static double arriving(const grid* G, const lattice* L, const double g[3],
+                       const double* drho, const double* ux, const double* uy, const double* uz,
+                       int k, int x, int y, int z, size_t i)
+{
+    size_t s;
+    double f;
+    if (link_source(G, L, k, x, y, z, &s)) {
+        f = feq_dev(L, L->inv[k], drho[i], ux[i] + g[0], uy[i] + g[1], uz[i] + g[2]);
+    } else {
+        f = feq_dev(L, k, drho[s], ux[s] + g[0], uy[s] + g[1], uz[s] + g[2]);
+    }
+    return f;
+}
+
+/* Constant-density (pressure) boundaries of Zou and He on the two faces of
+ * one non-periodic axis: bc = {axis (or -1: none), rho at coordinate 0,
+ * rho at coordinate n-1}. A fluid node on such a face keeps the given
+ * density; the populations entering from outside (c_axis pointing into the
+ * box) are unknown, the others arrive as in the interior (from fluid
+ * sources, or reflected at walls). Zou and He set the unknowns so that the
+ * node's moments are (rho_b, u) with u along the axis and
+ *     rho_b (1 - s u) = sum_{c_axis = 0} f + 2 sum_{c_axis = -s} f,
+ * s = +1 on the low face (inflow along +axis) and -1 on the high face, and
+ * the transverse velocity is zero. At tau = 1 the node's new state is those
+ * moments, so Tau1 needs only the known sums. With f = w + h (h the
+ * deviation) and sum_{c_axis=0} w + 2 sum_{c_axis=-s} w = 1:
+ *     u = s (rho_b - 1 - H0 - 2 Hout) / rho_b.
+ */
+static int zou_he_node(const grid* G, const lattice* L, const double g[3], const double* bc,
+                       const double* drho, const double* ux, const double* uy, const double* uz,
+                       int x, int y, int z, double out[4])
+{
+    int a = (int)bc[0];
+    if (a < 0 || a > 2) return 0;
+    int pos[3] = {x, y, z};
+    int n[3] = {G->nx, G->ny, G->nz};
+    double sgn;
+    double rho_b;
+    if (pos[a] == 0) { sgn = 1.0; rho_b = bc[1]; }
+    else if (pos[a] == n[a] - 1) { sgn = -1.0; rho_b = bc[2]; }
+    else return 0;
+    size_t i = idx3(G, x, y, z);
+    double h0 = 0.0, hout = 0.0;
+    for (int k = 0; k < L->q; ++k) {
+        int ck = L->c[k][a];
+        if ((double)ck == sgn) continue; /* unknown: enters from outside */
+        double f = arriving(G, L, g, drho, ux, uy, uz, k, x, y, z, i);
+        if (ck == 0) h0 += f;
+        else hout += f;
+    }
+    double u = sgn * ((rho_b - 1.0) - h0 - 2.0 * hout) / rho_b;
+    out[0] = rho_b - 1.0;
+    out[1] = out[2] = out[3] = 0.0;
+    out[1 + a] = u;
+    return 1;
+}
+
+static void tau1_node(const grid* G, const lattice* L, const double g[3], const double* bc,
                       const double* drho, const double* ux, const double* uy, const double* uz,
                       int x, int y, int z, double out[4])
 {
     size_t i = idx3(G, x, y, z);
     if (G->solid[i]) { out[0] = out[1] = out[2] = out[3] = 0.0; return; }
+    if (bc && zou_he_node(G, L, g, bc, drho, ux, uy, uz, x, y, z, out)) return;
     double d_acc = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
     for (int k = 0; k < L->q; ++k) {
-        size_t s;
-        double f;
-        if (link_source(G, L, k, x, y, z, &s)) {
-            /* halfway bounce-back: own previous rho*, u* in direction inv(k) */
-            f = feq_dev(L, L->inv[k], drho[i], ux[i] + g[0], uy[i] + g[1], uz[i] + g[2]);
-        } else {
-            f = feq_dev(L, k, drho[s], ux[s] + g[0], uy[s] + g[1], uz[s] + g[2]);
-        }
+        double f = arriving(G, L, g, drho, ux, uy, uz, k, x, y, z, i);
         d_acc += f;
         jx += (double)L->c[k][0] * f;
         jy += (double)L->c[k][1] * f;
@@ -196,34 +259,55 @@ static void tau1_node(const grid* G, const lattice* L, const double g[3],
 static int check_args(int q, int nx, int ny, int nz, lattice* L)
 {
     if (nx <= 0 || ny <= 0 || nz <= 0) return -1;
+    if (q == 9 && nz != 1) return -1; /* D2Q9: one plane */
     return lattice_make(q, L);
 }
 
-/* One Tau1 step over the whole box: (drho,ux,uy,uz) -> (*_o). */
-int orc_tau1_step(int q, int nx, int ny, int nz, const int* periodic, const double* g,
-                  const uint8_t* solid,
-                  const double* drho, const double* ux, const double* uy, const double* uz,
-                  double* drho_o, double* ux_o, double* uy_o, double* uz_o)
+/* A pressure boundary needs a non-periodic axis of the box (NULL: none). */
+static int check_bc(const double* bc, const int* periodic)
+{
+    if (!bc || bc[0] < 0.0) return 0;
+    int a = (int)bc[0];
+    if (a > 2 || periodic[a] || !(bc[1] > 0.0) || !(bc[2] > 0.0)) return -1;
+    return 0;
+}
+
+/* One Tau1 step over the whole box: (drho,ux,uy,uz) -> (*_o), with optional
+ * pressure faces bc (see zou_he_node; NULL or bc[0] < 0: none). */
+int orc_tau1_step_bc(int q, int nx, int ny, int nz, const int* periodic, const double* g, const double* bc,
+                     const uint8_t* solid,
+                     const double* drho, const double* ux, const double* uy, const double* uz,
+                     double* drho_o, double* ux_o, double* uy_o, double* uz_o)
 {
     lattice L;
-    if (check_args(q, nx, ny, nz, &L)) return -1;
+    if (check_args(q, nx, ny, nz, &L) || check_bc(bc, periodic)) return -1;
+    if (bc && bc[0] < 0.0) bc = NULL;
     grid G = {nx, ny, nz, {periodic[0], periodic[1], periodic[2]}, solid};
 #pragma omp parallel for schedule(static)
     for (int z = 0; z < nz; ++z)
         for (int y = 0; y < ny; ++y)
             for (int x = 0; x < nx; ++x) {
                 double o[4];
-                tau1_node(&G, &L, g, drho, ux, uy, uz, x, y, z, o);
+                tau1_node(&G, &L, g, bc, drho, ux, uy, uz, x, y, z, o);
                 size_t i = idx3(&G, x, y, z);
                 drho_o[i] = o[0]; ux_o[i] = o[1]; uy_o[i] = o[2]; uz_o[i] = o[3];
             }
     return 0;
 }
 
-/* nsteps Tau1 steps in place on (drho,ux,uy,uz), ping-pong with scratch. */
-int orc_tau1_run(int q, int nx, int ny, int nz, const int* periodic, const double* g,
-                 const uint8_t* solid, double* drho, double* ux, double* uy, double* uz,
-                 int64_t nsteps)
+int orc_tau1_step(int q, int nx, int ny, int nz, const int* periodic, const double* g,
+                  const uint8_t* solid,
+                  const double* drho, const double* ux, const double* uy, const double* uz,
+                  double* drho_o, double* ux_o, double* uy_o, double* uz_o)
+{
+    return orc_tau1_step_bc(q, nx, ny, nz, periodic, g, NULL, solid, drho, ux, uy, uz, drho_o, ux_o, uy_o, uz_o);
+}
+
+/* nsteps Tau1 steps in place on (drho,ux,uy,uz), ping-pong with scratch,
+ * with optional pressure faces bc. */
+int orc_tau1_run_bc(int q, int nx, int ny, int nz, const int* periodic, const double* g, const double* bc,
+                    const uint8_t* solid, double* drho, double* ux, double* uy, double* uz,
+                    int64_t nsteps)
 {
     size_t n = (size_t)nx * (size_t)ny * (size_t)nz;
     double* tmp = (double*)malloc(4 * n * sizeof(double));
@@ -232,14 +316,21 @@ int orc_tau1_run(int q, int nx, int ny, int nz, const int* periodic, const doubl
     double* b[4] = {tmp, tmp + n, tmp + 2 * n, tmp + 3 * n};
     int rc = 0;
     for (int64_t t = 0; t < nsteps && rc == 0; ++t) {
-        rc = orc_tau1_step(q, nx, ny, nz, periodic, g, solid, a[0], a[1], a[2], a[3],
-                           b[0], b[1], b[2], b[3]);
+        rc = orc_tau1_step_bc(q, nx, ny, nz, periodic, g, bc, solid, a[0], a[1], a[2], a[3],
+                              b[0], b[1], b[2], b[3]);
         for (int f = 0; f < 4; ++f) { double* s = a[f]; a[f] = b[f]; b[f] = s; }
     }
     if (nsteps % 2)  /* result sits in tmp: copy back */
         for (int f = 0; f < 4; ++f) memcpy(b[f], a[f], n * sizeof(double));
     free(tmp);
     return rc;
+}
+
+int orc_tau1_run(int q, int nx, int ny, int nz, const int* periodic, const double* g,
+                 const uint8_t* solid, double* drho, double* ux, double* uy, double* uz,
+                 int64_t nsteps)
+{
+    return orc_tau1_run_bc(q, nx, ny, nz, periodic, g, NULL, solid, drho, ux, uy, uz, nsteps);
 }
 
 /* One Tau1 step evaluated only at the listed flat node indices.
@@ -258,7 +349,7 @@ int orc_tau1_nodes(int q, int nx, int ny, int nz, const int* periodic, const dou
         int64_t i = nodes[m];
         if (i < 0 || i >= n) { out[4 * m] = out[4 * m + 1] = out[4 * m + 2] = out[4 * m + 3] = NAN; continue; }
         int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((int64_t)nx * ny));
-        tau1_node(&G, &L, g, drho, ux, uy, uz, x, y, z, out + 4 * m);
+        tau1_node(&G, &L, g, NULL, drho, ux, uy, uz, x, y, z, out + 4 * m);
     }
     return 0;
 }

@@ -441,3 +441,167 @@ def test_reduce_definitions():
     mags = np.sqrt(px ** 2 + st[2] ** 2 + st[3] ** 2)[fl]
     assert r["max_abs_u"] == pytest.approx(mags.max(), rel=1e-15)
     assert r["permeability"] == pytest.approx(oracle.NU * r["mean_ux_superficial"] / g[0], rel=1e-15)
+
+
+# --------------------------------------------------------------------------
+# D2Q9 (the 2D lattice of the paper's validation and first kernel, one plane)
+# --------------------------------------------------------------------------
+
+def test_d2q9_isotropy():
+    """D2Q9 weights and velocities: sum w = 1, sum w c = 0, sum w c c = I/3
+    and the fourth moment (d_ab d_cd + d_ac d_bd + d_ad d_bc)/9 in the plane
+    (Qian et al.), with inv(k) the opposite direction."""
+    c, w, inv = oracle.lattice(9)
+    cf = c[:, :2].astype(float)
+    assert np.all(c[:, 2] == 0)
+    assert abs(w.sum() - 1.0) < 1e-15
+    assert np.allclose(np.einsum("k,ka->a", w, cf), 0.0, atol=1e-16)
+    assert np.allclose(np.einsum("k,ka,kb->ab", w, cf, cf), np.eye(2) / 3, atol=1e-16)
+    d = np.eye(2)
+    m4 = np.einsum("k,ka,kb,kc,kd->abcd", w, cf, cf, cf, cf)
+    want = (np.einsum("ab,cd->abcd", d, d) + np.einsum("ac,bd->abcd", d, d) + np.einsum("ad,bc->abcd", d, d)) / 9
+    assert np.allclose(m4, want, atol=1e-16)
+    assert all(np.array_equal(c[inv[k]], -c[k]) for k in range(9))
+
+
+def test_d2q9_isolated_node_and_uniform_acceleration():
+    """Isolated fluid node (all 8 neighbours solid): rho' = rho, u' = -(u + g);
+    a wall-free periodic plane gains exactly g per step."""
+    solid = np.ones((1, 3, 3), np.uint8)
+    solid[0, 1, 1] = 0
+    g = (2e-5, -1e-5, 0.0)
+    D = oracle.Domain(9, solid, g=g)
+    st = [np.zeros(solid.shape) for _ in range(4)]
+    st[0][0, 1, 1], st[1][0, 1, 1], st[2][0, 1, 1] = 0.015, 0.004, -0.007
+    o = D.tau1_step(st)
+    assert abs(o[0][0, 1, 1] - 0.015) < 1e-17
+    assert abs(o[1][0, 1, 1] + (0.004 + g[0])) < 1e-17 and abs(o[2][0, 1, 1] + (-0.007 + g[1])) < 1e-17
+    shape = (1, 5, 7)
+    u0 = (0.01, -0.02)
+    st = (np.full(shape, 0.02), np.full(shape, u0[0]), np.full(shape, u0[1]), np.zeros(shape))
+    D = oracle.Domain(9, np.zeros(shape, np.uint8), g=g)
+    out = D.tau1_run(st, 40)
+    assert np.max(np.abs(out[0] - 0.02)) < 1e-15
+    for a in range(2):
+        assert np.max(np.abs(out[1 + a] - (u0[a] + 40 * g[a]))) < 1e-14
+    assert np.all(out[3] == 0)
+
+
+def test_d2q9_channel_recurrence_and_steady_profile():
+    """A plane channel (solid rows y = 0 and y = 31, periodic in x) reduces to
+    the same 1D recurrence as the 3D channel: the D2Q9 layers c_y = -1, 0, 1
+    have sums of w c_x^2 of 1/18, 2/9, 1/18. At t = 1000 and at steady state
+    (u = 3 g (y - 1/2)(30.5 - y) - g/4)."""
+    g = 1e-6
+    solid = np.zeros((1, 32, 3), np.uint8)
+    solid[0, 0, :] = 1
+    solid[0, 31, :] = 1
+    D = oracle.Domain(9, solid, periodic=(1, 0, 1), g=(g, 0, 0))
+    out = D.tau1_run(D.zero_state(), 1000)
+    ref = channel_recurrence(32, g, 1000)
+    assert np.max(np.abs(out[1][0, :, 0] - ref)) <= 1e-12 * np.max(np.abs(ref))
+    assert np.max(np.abs(out[2])) < 1e-18
+    out = D.tau1_run(out, 19000)
+    y = np.arange(1, 31, dtype=np.float64)
+    exact = 3 * g * (y - 0.5) * (30.5 - y) - g / 4
+    assert np.max(np.abs(out[1][0, 1:31, 1] - exact)) <= 1e-12 * np.max(exact)
+
+
+def test_d2q9_mass_and_bgk():
+    """D2Q9 on a random porous plane: fluid mass conserved to 1e-12 over 500
+    steps, and Tau1 equals pull BGK at tau = 1 to rounding at every step."""
+    solid = lbm_inputs.random_mask(17, 13, 1, 0.25, 51)
+    st = lbm_inputs.random_fields(solid.shape, 52, 2e-3, 3e-3, solid)
+    st = (st[0], st[1], st[2], np.zeros(solid.shape))
+    g = (1e-5, -3e-6, 0.0)
+    D = oracle.Domain(9, solid, periodic=(1, 0, 1), g=g)
+    m0 = math.fsum(st[0][solid == 0])
+    out = D.tau1_run(st, 500)
+    assert abs(math.fsum(out[0][solid == 0]) - m0) <= 1e-12 * int(np.count_nonzero(solid == 0))
+    h = D.bgk_init(st, 1.0)
+    t = st
+    worst = 0.0
+    for _ in range(100):
+        t = D.tau1_step(t)
+        h, b = D.bgk_step(h, 1.0)
+        worst = max(worst, max(float(np.max(np.abs(t[a] - b[a]))) for a in range(3)))
+    assert worst < 1e-16, worst
+
+
+# --------------------------------------------------------------------------
+# constant-density (Zou-He) faces: the pressure-driven channel of the
+# paper's 2D validation (rho_in / rho_out at the inlet and outlet)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("q,axis", [(9, 0), (9, 1), (19, 0), (19, 1), (19, 2), (27, 2)])
+@pytest.mark.parametrize("u0", [2e-3, -1.5e-3])
+def test_zou_he_uniform_flow_is_fixed_point(q, axis, u0):
+    """A uniform flow (rho_b, u0 along the axis) between two faces held at the
+    same density rho_b is a fixed point: the known populations are
+    equilibria of (rho_b, u0), and the Zou-He relation
+    rho_b (1 - s u) = sum_{c=0} f + 2 sum_{c=-s} f holds for them at u = u0
+    on both faces (s = +1 inflow face, -1 outflow face)."""
+    shape = [1, 4, 9] if q == 9 else [5, 4, 6]
+    if q == 9 and axis == 1:
+        shape = [1, 9, 4]
+    solid = np.zeros(shape, np.uint8)
+    per = [1, 1, 1]
+    per[axis] = 0
+    rho_b = 1.02
+    st = [np.full(shape, rho_b - 1.0), np.zeros(shape), np.zeros(shape), np.zeros(shape)]
+    st[1 + axis][:] = u0
+    D = oracle.Domain(q, solid, periodic=per, pressure=(axis, rho_b, rho_b))
+    out = D.tau1_run(st, 25)
+    for a in range(4):
+        assert np.max(np.abs(out[a] - st[a])) < 1e-15, (a, np.max(np.abs(out[a] - st[a])))
+
+
+def test_zou_he_faces_hold_density_and_normal_flow():
+    """After any step the fluid nodes of the two faces hold rho_in and rho_out
+    exactly and move only along the axis; solid face nodes stay solid."""
+    solid = lbm_inputs.random_mask(12, 10, 1, 0.2, 61)
+    rin, rout = 1.01, 0.99
+    D = oracle.Domain(9, solid, periodic=(0, 1, 1), pressure=(0, rin, rout))
+    out = D.tau1_run(D.zero_state(), 37)
+    fl = solid[0] == 0
+    assert np.all(out[0][0, fl[:, 0], 0] == rin - 1.0)
+    assert np.all(out[0][0, fl[:, -1], -1] == rout - 1.0)
+    for x in (0, -1):
+        assert np.all(out[2][0, :, x] == 0.0) and np.all(out[3][0, :, x] == 0.0)
+    assert np.all(out[0][solid != 0] == 0.0)
+
+
+@pytest.mark.parametrize("q", [9, 19])
+def test_zou_he_channel_matches_poiseuille(q):
+    """Pressure-driven channel, run to steady state: H = 20 fluid rows between
+    halfway bounce-back walls (wall positions at 1/2 and 20.5), faces at
+    x = 0 and x = 59 held at rho = 1.001 and 0.999. At x = 30 the profile is
+    the continuum Eq. (poiseuile), u(y) = (-dp/dx) y'(H - y') / (2 rho nu) with
+    y' = y - 1/2, p = rho / 3 and nu = 1/6 (the flow runs from high to low
+    pressure), within a mean absolute percentage error of 0.5 %, symmetric
+    about the channel centre, and steady."""
+    nx, nw = 60, 22
+    if q == 9:
+        solid = np.zeros((1, nw, nx), np.uint8)
+        solid[0, 0, :] = 1
+        solid[0, nw - 1, :] = 1
+        per = (0, 0, 1)
+    else:
+        solid = np.zeros((nw, 1, nx), np.uint8)
+        solid[0] = 1
+        solid[nw - 1] = 1
+        per = (0, 1, 0)
+    rin, rout = 1.001, 0.999
+    D = oracle.Domain(q, solid, periodic=per, pressure=(0, rin, rout))
+    out = D.tau1_run(D.zero_state(), 30000)
+    nxt = D.tau1_step(out)
+    assert np.max(np.abs(nxt[1] - out[1])) < 1e-13
+    prof = (out[1][0, 1:nw - 1, 30] if q == 9 else out[1][1:nw - 1, 0, 30])
+    rho = 1.0 + float(np.mean(out[0][0, 1:nw - 1, 30] if q == 9 else out[0][1:nw - 1, 0, 30]))
+    H = nw - 2
+    yp = np.arange(1, nw - 1, dtype=np.float64) - 0.5
+    dpdx = (rout - rin) / 3.0 / (nx - 1)
+    ana = -dpdx / (2.0 * rho * oracle.NU) * yp * (H - yp)
+    mape = float(np.mean(np.abs(prof - ana) / ana))
+    assert mape < 5e-3, mape
+    assert np.max(np.abs(prof - prof[::-1])) < 1e-15
