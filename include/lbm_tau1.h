@@ -56,7 +56,9 @@ typedef enum {
     LBM_ESTATE = 7      /* call out of order (e.g. step before set_geometry) */
 } lbm_status;
 
-typedef enum { LBM_D3Q19 = 19, LBM_D3Q27 = 27 } lbm_lattice;
+/* D2Q9 is one plane (nz = 1): the paper's 2D lattice (Section 3.1), dense
+ * layout and Tau1 scheme only. */
+typedef enum { LBM_D2Q9 = 9, LBM_D3Q19 = 19, LBM_D3Q27 = 27 } lbm_lattice;
 
 /* Storage of drho and u in device memory. F16S and BF16S hold each field
  * times a power-of-two scale in 16 bits and compute in FP32. */
@@ -171,11 +173,30 @@ const char* lbm_tau1_last_error(const lbm_tau1* h);
 /* Number of device kernel launches queued by this handle since creation. */
 int64_t lbm_tau1_launch_count(const lbm_tau1* h);
 
+/* Constant-density (pressure) faces on a non-periodic axis (Section 3.3: the
+ * 2D validation channel is driven by rho_in at the inlet and rho_out at the
+ * outlet, with the boundary conditions of Zou and He). The fluid nodes of the
+ * face at coordinate 0 of `axis` keep density rho_lo and those of the face
+ * at n - 1 keep rho_hi; after every step each such node takes the velocity
+ * along the axis that the Zou-He relation gives from the populations arriving
+ * from inside (its known populations: equilibria of fluid sources, halfway
+ * bounce-back at walls), u = s (rho_b - 1 - H0 - 2 Hout) / rho_b with s = +1
+ * on the low face and -1 on the high face, H0 and Hout the deviations from
+ * the weights summed over the known directions parallel to the face and
+ * pointing out of the box; the velocity across the axis is zero. Meant for
+ * g = 0 (pressure-driven flow). axis = -1 removes the faces. Dense layout,
+ * Tau1 scheme; D2Q9 takes axis 0 or 1. Errors: LBM_EINVAL (axis out of range
+ * or periodic, a density not finite and positive, sparse layout or BGK). */
+lbm_status lbm_tau1_set_pressure(lbm_tau1* h, int32_t axis, double rho_lo, double rho_hi);
+
 /* ---- Tile-shape autotuning (no counterpart in the paper, whose CPU kernels
- * fix the chunk shape at compile time, Section 3.2). The tiled kernel comes in
- * variants: a tile shape (tile height, resident blocks per SM) and the number
- * of z planes a block steps (variants [0, n/2) step 24 planes per block,
- * [n/2, n) 32, n = lbm_tau1_variant_count). The default is variant 0. */
+ * fix the chunk shape at compile time, Section 3.2). The tiled kernel of the
+ * 3D lattices comes in variants: [0, 2R) the row-pair form (R tile shapes:
+ * warps per block, resident blocks per SM; [0, R) step 24 z planes per block,
+ * [R, 2R) 32), used when nx is a multiple of 32 and ny of the tile height,
+ * else the pair-position form of the same chunk height; [2R, 2R + 2T) the
+ * pair-position form (T shapes, same chunk rule), TMA-staged when its tiles
+ * are full. All variants give the same bits. The default is variant 0. */
 
 /* Number of variants of the handle's step kernel (1 if it has none). */
 int32_t lbm_tau1_variant_count(const lbm_tau1* h);

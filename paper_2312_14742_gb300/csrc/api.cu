@@ -44,6 +44,8 @@ struct lbm_tau1 {
     int* nbr = nullptr;         // sparse: neighbour table [(q-1)][nf]
     int64_t launches = 0;
     unsigned int* dtimeouts = nullptr;  // device counter of staged-copy waits that ran out
+    int p_axis = -1;            // constant-density faces on this axis (-1: none)
+    double p_lo = 1.0, p_hi = 1.0;
     std::string err;
 };
 
@@ -138,6 +140,7 @@ void fill_args(const lbm_tau1* h, StepArgs& a)
 
 int variant_count(const lbm_tau1* h)
 {
+    if (h->cfg.q == LBM_D2Q9) return 1;
     return (!h->bgk && h->kernel == LBM_KERNEL_TILED) ? tau1_tiled_variants(h->cfg.q, h->cfg.storage) : 1;
 }
 
@@ -282,6 +285,7 @@ lbm_status build_fluid_list(lbm_tau1* h)
 
 cudaError_t launch_kernel(const lbm_tau1* h, int variant, const StepArgs& a)
 {
+    if (h->cfg.q == LBM_D2Q9) return launch_tau1_2d(h->kernel == LBM_KERNEL_SIMPLE, h->cfg.storage, a, h->stream);
     if (h->sparse) return launch_tau1_sparse(h->cfg.q, h->cfg.storage, a, (int)h->nf, h->nbr, h->stream);
     if (h->kernel == LBM_KERNEL_TILED) return launch_tau1_tiled(h->cfg.q, h->cfg.storage, variant, a, h->stream);
     return launch_tau1_simple(h->cfg.q, h->cfg.storage, a, h->stream);
@@ -303,6 +307,11 @@ lbm_status launch_step(lbm_tau1* h)
     cudaError_t e = launch_kernel(h, h->variant, a);
     if (e != cudaSuccess) return cuda_fail(h, e, "tau1 step launch");
     ++h->launches;
+    if (h->p_axis >= 0) {
+        e = launch_zou_he(h->cfg.q, h->cfg.storage, a, h->p_axis, h->p_lo, h->p_hi, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "pressure-face launch");
+        ++h->launches;
+    }
     h->cur ^= 1;
     ++h->step;
     if (h->dscale && h->step % RESCALE_EVERY == 0) {
@@ -350,7 +359,10 @@ lbm_status lbm_tau1_create(const lbm_tau1_config* cfg, lbm_tau1** out)
 {
     if (out) *out = nullptr;
     if (!cfg || !out) return fail(nullptr, LBM_EINVAL, "create: NULL argument");
-    if (cfg->q != 19 && cfg->q != 27) return fail(nullptr, LBM_EINVAL, "create: q must be 19 or 27");
+    if (cfg->q != LBM_D2Q9 && cfg->q != 19 && cfg->q != 27)
+        return fail(nullptr, LBM_EINVAL, "create: q must be 9, 19 or 27");
+    if (cfg->q == LBM_D2Q9 && (cfg->nz != 1 || cfg->layout != LBM_DENSE || cfg->scheme != LBM_SCHEME_TAU1))
+        return fail(nullptr, LBM_EINVAL, "create: D2Q9 takes one plane (nz = 1), the dense layout and the Tau1 scheme");
     if (storage_node_bytes(cfg->storage) == 0) return fail(nullptr, LBM_EINVAL, "create: bad storage");
     if (cfg->nx < 1 || cfg->ny < 1 || cfg->nz < 1) return fail(nullptr, LBM_EINVAL, "create: box sizes must be >= 1");
     if (cfg->layout != LBM_DENSE && cfg->layout != LBM_SPARSE) return fail(nullptr, LBM_EINVAL, "create: bad layout");
@@ -377,7 +389,7 @@ lbm_status lbm_tau1_create(const lbm_tau1_config* cfg, lbm_tau1** out)
     h->kernel = cfg->kernel;
     h->sparse = cfg->layout == LBM_SPARSE;
     if (h->sparse) h->kernel = LBM_KERNEL_SIMPLE;  // one thread per fluid node; no tile variants
-    const bool tiled_ok = tau1_tiled_supported(cfg->q, cfg->storage, n);
+    const bool tiled_ok = cfg->q == LBM_D2Q9 || tau1_tiled_supported(cfg->q, cfg->storage, n);
     if (h->kernel == LBM_KERNEL_AUTO) h->kernel = tiled_ok ? LBM_KERNEL_TILED : LBM_KERNEL_SIMPLE;
     if (h->kernel == LBM_KERNEL_TILED && !tiled_ok) {
         delete h;
@@ -581,6 +593,25 @@ lbm_status lbm_tau1_step(lbm_tau1* h, int64_t nsteps)
     if (!h->has_geometry) return fail(h, LBM_ESTATE, "step: call set_geometry first");
     for (int64_t t = 0; t < nsteps; ++t)
         if (lbm_status st = launch_step(h)) return st;
+    return LBM_OK;
+}
+
+lbm_status lbm_tau1_set_pressure(lbm_tau1* h, int32_t axis, double rho_lo, double rho_hi)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "set_pressure: NULL handle");
+    if (axis < 0) {
+        h->p_axis = -1;
+        return LBM_OK;
+    }
+    const int dims = h->cfg.q == LBM_D2Q9 ? 2 : 3;
+    if (axis >= dims) return fail(h, LBM_EINVAL, "set_pressure: axis out of range");
+    if (h->cfg.periodic[axis]) return fail(h, LBM_EINVAL, "set_pressure: the axis must not be periodic");
+    if (h->sparse || h->bgk) return fail(h, LBM_EINVAL, "set_pressure: dense layout and Tau1 scheme only");
+    if (!(std::isfinite(rho_lo) && std::isfinite(rho_hi) && rho_lo > 0.0 && rho_hi > 0.0))
+        return fail(h, LBM_EINVAL, "set_pressure: densities must be finite and positive");
+    h->p_axis = axis;
+    h->p_lo = rho_lo;
+    h->p_hi = rho_hi;
     return LBM_OK;
 }
 

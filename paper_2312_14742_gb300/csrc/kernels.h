@@ -27,6 +27,14 @@ int tau1_rowpair_shapes(int storage);
 bool tau1_rowpair_ok(int q, int storage, int shape, const StepArgs& a);
 cudaError_t launch_tau1_rowpair(int q, int storage, int shape, int zchunk, const StepArgs& a, cudaStream_t s);
 
+// D2Q9 (one plane): simple = one thread per node, else the y-marching warp
+// kernel; same bits.
+cudaError_t launch_tau1_2d(bool simple, int storage, const StepArgs& a, cudaStream_t s);
+// Constant-density (Zou-He) faces of a non-periodic axis: overwrites the face
+// nodes of a.post after a step from a.pre (q = 9, 19 or 27).
+cudaError_t launch_zou_he(int q, int storage, const StepArgs& a, int axis, double rho_lo, double rho_hi,
+                          cudaStream_t s);
+
 // Sparse layout (fluid list + neighbour table). count: counts[0..nb) become
 // the exclusive prefix sums of the fluid counts of the scan blocks and
 // counts[nb] the total; build: idx (n ints) and pos (nf ints), then nbr

@@ -42,4 +42,28 @@ template <> struct Weights<27> {
     }
 };
 
+// D2Q9 (one plane): rest; (+1,0), (-1,0), (0,+1), (0,-1); (+1,+1), (-1,-1),
+// (+1,-1), (-1,+1). inv(k) = k + 1 for odd k, k - 1 for even k. Weights by
+// class (rest, axis, diagonal): 4/9, 1/9, 1/36.
+__host__ __device__ constexpr int c2(int k, int a)
+{
+    constexpr int T[9][2] = {{0, 0}, {1, 0}, {-1, 0}, {0, 1}, {0, -1}, {1, 1}, {-1, -1}, {1, -1}, {-1, 1}};
+    return a < 2 ? T[k][a] : 0;
+}
+__host__ __device__ constexpr int inv2(int k) { return k == 0 ? 0 : ((k & 1) ? k + 1 : k - 1); }
+__host__ __device__ constexpr int class2(int k) { return k == 0 ? 0 : (k < 5 ? 1 : 2); }
+__host__ __device__ constexpr double w2(int cls) { return cls == 0 ? 4.0 / 9.0 : (cls == 1 ? 1.0 / 9.0 : 1.0 / 36.0); }
+
+// One interface to the three lattices: velocity component, opposite, weight.
+template <int Q> struct Lat {
+    __host__ __device__ static constexpr int c(int k, int a) { return cvel(k, a); }
+    __host__ __device__ static constexpr int inv(int k) { return inv_dir(k); }
+    __host__ __device__ static constexpr double w(int k) { return Weights<Q>::w(dir_class(k)); }
+};
+template <> struct Lat<9> {
+    __host__ __device__ static constexpr int c(int k, int a) { return c2(k, a); }
+    __host__ __device__ static constexpr int inv(int k) { return inv2(k); }
+    __host__ __device__ static constexpr double w(int k) { return w2(class2(k)); }
+};
+
 }  // namespace lbm

@@ -7,7 +7,7 @@ namespace lbm {
 // flags[i] = FLAG_SOLID for solid nodes; FLAG_WALL_LINK for fluid nodes that
 // have at least one wall link (a solid x - c_k, or one across a non-periodic
 // face); 0 otherwise.
-template <int Q>
+template <int Q, bool PLANE = false>
 __global__ void build_flags_kernel(int nx, int ny, int nz, int px, int py, int pz, const uint8_t* __restrict__ solid,
                                    uint8_t* __restrict__ flags)
 {
@@ -18,6 +18,7 @@ __global__ void build_flags_kernel(int nx, int ny, int nz, int px, int py, int p
         bool wall = false;
         static_for<1, Q>([&](auto kc) {
             constexpr int K = decltype(kc)::value;
+            if constexpr (PLANE && cvel(K, 2) != 0) return;  // D2Q9: the in-plane directions of D3Q19
             int sx = x - cvel(K, 0), sy = y - cvel(K, 1), sz = z - cvel(K, 2);
             bool out = false;
             if (sx < 0 || sx >= nx) { if (px) sx = sx < 0 ? sx + nx : sx - nx; else out = true; }
@@ -40,7 +41,10 @@ cudaError_t launch_build_flags(int q, int nx, int ny, int nz, const int periodic
                                uint8_t* flags, cudaStream_t s)
 {
     const int64_t n = (int64_t)nx * ny * nz;
-    if (q == 19)
+    if (q == 9)
+        build_flags_kernel<19, true><<<grid_for(n, 256), 256, 0, s>>>(nx, ny, nz, periodic[0], periodic[1],
+                                                                       periodic[2], solid, flags);
+    else if (q == 19)
         build_flags_kernel<19><<<grid_for(n, 256), 256, 0, s>>>(nx, ny, nz, periodic[0], periodic[1], periodic[2],
                                                                  solid, flags);
     else if (q == 27)

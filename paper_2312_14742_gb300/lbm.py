@@ -20,7 +20,7 @@ LIB_PATH = _build.LIB
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EDIVERGED, LBM_ETIMEOUT, LBM_EBUSY, LBM_ESTATE = range(8)
 STATUS_NAMES = ["LBM_OK", "LBM_EINVAL", "LBM_ENOMEM", "LBM_ECUDA", "LBM_EDIVERGED", "LBM_ETIMEOUT", "LBM_EBUSY",
                 "LBM_ESTATE"]
-LBM_D3Q19, LBM_D3Q27 = 19, 27
+LBM_D2Q9, LBM_D3Q19, LBM_D3Q27 = 9, 19, 27
 LBM_F64, LBM_F32, LBM_F16S, LBM_BF16S = range(4)
 STORAGE = {"f64": LBM_F64, "f32": LBM_F32, "f16s": LBM_F16S, "bf16s": LBM_BF16S}
 LBM_DENSE, LBM_SPARSE = 0, 1
@@ -73,6 +73,7 @@ SIGNATURES = {
     "lbm_tau1_destroy": (_I, [_H]),
     "lbm_tau1_last_error": (ctypes.c_char_p, [_H]),
     "lbm_tau1_launch_count": (_I64, [_H]),
+    "lbm_tau1_set_pressure": (_I, [_H, ctypes.c_int32, ctypes.c_double, ctypes.c_double]),
     "lbm_tau1_variant_count": (ctypes.c_int32, [_H]),
     "lbm_tau1_set_variant": (_I, [_H, ctypes.c_int32]),
     "lbm_tau1_autotune": (_I, [_H, ctypes.c_int32, _P, _P]),
@@ -172,6 +173,10 @@ def lbm_tau1_last_error(h) -> str:
 
 def lbm_tau1_launch_count(h) -> int:
     return _fn("lbm_tau1_launch_count")(h)
+
+
+def lbm_tau1_set_pressure(h, axis: int, rho_lo: float, rho_hi: float) -> int:
+    return _fn("lbm_tau1_set_pressure")(h, axis, rho_lo, rho_hi)
 
 
 def lbm_tau1_variant_count(h) -> int:
@@ -328,6 +333,10 @@ class Tau1:
 
     def step(self, nsteps: int = 1) -> None:
         self._check(lbm_tau1_step(self.h, int(nsteps)))
+
+    def set_pressure(self, axis: int, rho_lo: float, rho_hi: float) -> None:
+        """Constant-density (Zou-He) faces on a non-periodic axis (-1: none)."""
+        self._check(lbm_tau1_set_pressure(self.h, int(axis), float(rho_lo), float(rho_hi)))
 
     def reduce(self, allow_diverged: bool = False) -> dict:
         s = lbm_tau1_stats()
