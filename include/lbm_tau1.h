@@ -189,6 +189,20 @@ int64_t lbm_tau1_launch_count(const lbm_tau1* h);
  * or periodic, a density not finite and positive, sparse layout or BGK). */
 lbm_status lbm_tau1_set_pressure(lbm_tau1* h, int32_t axis, double rho_lo, double rho_hi);
 
+/* Halo exchange of a z-slab decomposition (nodes are independent within a
+ * step, Section 2.1.2, so a box split into z-slabs needs, per step, only the
+ * plane on each side of every cut). Copies plane z of the current state, as
+ * the handle stores it (nx*ny records in the storage format: 32, 16 or 8
+ * bytes each, solid nodes marked), between the handle and the device buffer
+ * buf of nx*ny*record bytes: to_handle = 0 reads the plane into buf, 1
+ * writes buf into the plane. Queued on the handle's stream without waiting.
+ * A slab holds its planes plus one halo plane below and one above; before
+ * each step the halo planes receive the neighbours' edge planes. Dense
+ * layout, Tau1 scheme, F64, F32 or BF16S storage (F16 records carry the
+ * handle's own scales). Errors: LBM_EINVAL, LBM_ESTATE (no geometry),
+ * LBM_ECUDA. */
+lbm_status lbm_tau1_copy_plane(lbm_tau1* h, int32_t z, void* buf, int32_t to_handle);
+
 /* ---- Tile-shape autotuning (no counterpart in the paper, whose CPU kernels
  * fix the chunk shape at compile time, Section 3.2). The tiled kernel of the
  * 3D lattices comes in variants: [0, 2R) the row-pair form (R tile shapes:

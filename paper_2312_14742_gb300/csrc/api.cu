@@ -615,6 +615,23 @@ lbm_status lbm_tau1_set_pressure(lbm_tau1* h, int32_t axis, double rho_lo, doubl
     return LBM_OK;
 }
 
+lbm_status lbm_tau1_copy_plane(lbm_tau1* h, int32_t z, void* buf, int32_t to_handle)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "copy_plane: NULL handle");
+    if (!buf) return fail(h, LBM_EINVAL, "copy_plane: NULL buffer");
+    if (h->sparse || h->bgk) return fail(h, LBM_EINVAL, "copy_plane: dense layout and Tau1 scheme only");
+    if (h->cfg.storage == LBM_F16S)
+        return fail(h, LBM_EINVAL, "copy_plane: FP16 records carry the handle's own scales; use F32, F64 or BF16S");
+    if (z < 0 || z >= h->cfg.nz) return fail(h, LBM_EINVAL, "copy_plane: plane out of range");
+    if (!h->has_geometry) return fail(h, LBM_ESTATE, "copy_plane: call set_geometry first");
+    if (lbm_status st = check_ptr(h, buf, 1, "copy_plane buffer")) return st;
+    const size_t plane = (size_t)h->cfg.nx * (size_t)h->cfg.ny * h->node_bytes;
+    unsigned char* base = static_cast<unsigned char*>(h->buf[h->cur]) + (size_t)z * plane;
+    LBM_CUDA(h, cudaMemcpyAsync(to_handle ? static_cast<void*>(base) : buf, to_handle ? buf : base, plane,
+                                cudaMemcpyDeviceToDevice, h->stream), "copy_plane: copy");
+    return LBM_OK;
+}
+
 int32_t lbm_tau1_variant_count(const lbm_tau1* h) { return h ? variant_count(h) : 0; }
 
 lbm_status lbm_tau1_set_variant(lbm_tau1* h, int32_t variant)

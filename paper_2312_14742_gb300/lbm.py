@@ -74,6 +74,7 @@ SIGNATURES = {
     "lbm_tau1_last_error": (ctypes.c_char_p, [_H]),
     "lbm_tau1_launch_count": (_I64, [_H]),
     "lbm_tau1_set_pressure": (_I, [_H, ctypes.c_int32, ctypes.c_double, ctypes.c_double]),
+    "lbm_tau1_copy_plane": (_I, [_H, ctypes.c_int32, _P, ctypes.c_int32]),
     "lbm_tau1_variant_count": (ctypes.c_int32, [_H]),
     "lbm_tau1_set_variant": (_I, [_H, ctypes.c_int32]),
     "lbm_tau1_autotune": (_I, [_H, ctypes.c_int32, _P, _P]),
@@ -177,6 +178,10 @@ def lbm_tau1_launch_count(h) -> int:
 
 def lbm_tau1_set_pressure(h, axis: int, rho_lo: float, rho_hi: float) -> int:
     return _fn("lbm_tau1_set_pressure")(h, axis, rho_lo, rho_hi)
+
+
+def lbm_tau1_copy_plane(h, z: int, buf, to_handle: int) -> int:
+    return _fn("lbm_tau1_copy_plane")(h, z, buf, to_handle)
 
 
 def lbm_tau1_variant_count(h) -> int:
@@ -333,6 +338,11 @@ class Tau1:
 
     def step(self, nsteps: int = 1) -> None:
         self._check(lbm_tau1_step(self.h, int(nsteps)))
+
+    def copy_plane(self, z: int, buf, to_handle: bool) -> None:
+        """Raw records of plane z of the current state to (to_handle False) or
+        from (True) a device buffer (a torch CUDA tensor of nx*ny*record bytes)."""
+        self._check(lbm_tau1_copy_plane(self.h, int(z), _ptr(buf, True), 1 if to_handle else 0))
 
     def set_pressure(self, axis: int, rho_lo: float, rho_hi: float) -> None:
         """Constant-density (Zou-He) faces on a non-periodic axis (-1: none)."""
