@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 import lbm_inputs
+from oracle_steady import oracle_to_steady
 from paper_2312_14742_gb300 import Tau1, build
 
 pytestmark = pytest.mark.gpu
@@ -125,10 +126,12 @@ def test_channel_steady_profile(storage):
 @pytest.mark.parametrize("storage", ("f16s", "bf16s"))
 def test_porous_permeability_within_one_percent(storage):
     """Porosity 0.5 medium (the 512^3 workload's kind at 48^3): steady-state
-    permeability with 16-bit storage within 1% of the FP64 run."""
+    permeability and max|u| with 16-bit storage against the FP64 oracle run
+    to the same steady state (relative change of the mean velocity below
+    1e-7 over 100 steps): permeability within 1 %, max|u| within 2 %."""
     solid, info = lbm_inputs.sphere_pack(48, 48, 48, 5.0, 0.5, lbm_inputs.workload_seed(3, 48))
     g = (1e-5, 0.0, 0.0)
-    ref, fref, steps = run_to_steady(19, solid, (1, 1, 1), g, tol=1e-7)
+    ref, fref, steps = oracle_to_steady(19, solid, (1, 1, 1), g, tol=1e-7)
     got, fgot = run_averaged(19, solid, (1, 1, 1), g, storage, steps)
     assert abs(got["permeability"] - ref["permeability"]) <= 1e-2 * abs(ref["permeability"])
     assert abs(got["max_abs_u"] - ref["max_abs_u"]) <= 2e-2 * ref["max_abs_u"]

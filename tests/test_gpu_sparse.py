@@ -81,12 +81,13 @@ def test_sparse_all_solid_and_single_fluid_node():
 
 @pytest.mark.parametrize("storage", ("f16s", "bf16s"))
 def test_sparse_16bit_permeability(storage):
+    """Sparse layout with 16-bit storage: permeability averaged over 10 states
+    50 steps apart after 1500 steps, within 1 % of the FP64 oracle's over the
+    same window."""
     solid, _ = lbm_inputs.sphere_pack(40, 40, 40, 4.0, 0.5, lbm_inputs.workload_seed(3, 40))
     g = (1e-5, 0, 0)
-    with Tau1(19, (40, 40, 40), storage="f64", g=g, layout=LBM_SPARSE) as t:
-        t.set_geometry(solid)
-        t.step(2000)
-        k64 = t.reduce()["permeability"]
+    from oracle_steady import oracle_window
+    k64 = oracle_window(19, solid, (1, 1, 1), g, 1500)
     with Tau1(19, (40, 40, 40), storage=storage, g=g, layout=LBM_SPARSE) as t:
         t.set_geometry(solid)
         t.step(1500)
