@@ -70,7 +70,18 @@ typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16S = 2, LBM_BF16S = 3 } lbm_stora
  * table are built by set_geometry (4 (q-1) + 4 bytes per fluid node). The
  * sparse layout is for the Tau1 scheme, boxes of fewer than 2^31 nodes; its
  * FP32 and FP64 results equal the dense kernels' bits. */
-typedef enum { LBM_DENSE = 0, LBM_SPARSE = 1 } lbm_layout;
+/* COMPACT: the dense records, with each step's work split by tile column
+ * (32 x H x 24 nodes, H the tiled kernel's tile height): tile columns without
+ * fluid are never read or written; those whose fluid fraction is at least the
+ * threshold f* are stepped by the tiled kernel through a list; the fluid
+ * nodes of the others are stepped one thread per node through a 4-byte list
+ * of box indices. set_geometry builds the lists (f* = 0.3 unless set by
+ * lbm_tau1_set_compact_threshold; lbm_tau1_autotune times a few thresholds).
+ * Tau1 scheme, D3Q19 or D3Q27, boxes of fewer than 2^31 nodes; FP32 and FP64
+ * results equal the dense kernels' bits (solid nodes keep their marker).
+ * Every tile column goes to the node list when nx is not a multiple of 32 or
+ * ny not of H. */
+typedef enum { LBM_DENSE = 0, LBM_SPARSE = 1, LBM_COMPACT = 2 } lbm_layout;
 
 /* LBM_SCHEME_TAU1 is the method. LBM_SCHEME_BGK is the standard pull BGK at
  * tau = 1 with stored populations in SoA form (Algorithm "Standard LBM",
@@ -223,7 +234,12 @@ lbm_status lbm_tau1_set_variant(lbm_tau1* h, int32_t variant);
  * and returns its index in *chosen and its time per step in *ms_per_step
  * (either may be NULL). The trial launches rewrite only the scratch copy, so
  * the state and step counter are unchanged. Synchronises the stream.
+ * Compact layout: times the thresholds f* of LBM_TAU1_COMPACT_THRESHOLDS
+ * instead, rebuilding the lists for each, keeps the fastest and returns its
+ * index in that list; the cache is not used (the best f* depends on the
+ * medium).
  * Errors: LBM_EINVAL (trials < 1), LBM_ESTATE (no geometry), LBM_ECUDA. */
+#define LBM_TAU1_COMPACT_THRESHOLDS {0.0, 0.1, 0.2, 0.3, 0.4, 0.5, 0.7, 1.01}
 lbm_status lbm_tau1_autotune(lbm_tau1* h, int32_t trials, int32_t* chosen, float* ms_per_step);
 
 /* Autotune cache for the whole process: path of a JSON file of chosen
@@ -234,6 +250,31 @@ lbm_status lbm_tau1_autotune(lbm_tau1* h, int32_t trials, int32_t* chosen, float
  * times the variants and writes its choice to the file. NULL or "" turns the
  * cache off (the default). The file is read and rewritten on each use. */
 void lbm_tau1_set_tune_cache(const char* path);
+
+/* Compact layout (LBM_COMPACT): how set_geometry split the box. */
+typedef struct lbm_tau1_compact_info {
+    double threshold;        /* f*: fluid fraction from which a tile column is tiled */
+    int32_t tile[3];         /* tile column: 32, H, z chunk (24, or nz if smaller) */
+    int32_t tiled_ok;        /* 1 if the tiled kernel can take tile columns */
+    int64_t columns;         /* tile columns of the box */
+    int64_t empty_columns;   /* without a fluid node: never visited */
+    int64_t full_columns;    /* every node fluid */
+    int64_t tiled_columns;   /* stepped by the tiled kernel */
+    int64_t listed_columns;  /* whose fluid nodes are in the node list */
+    int64_t tiled_nodes;     /* box nodes of the tiled columns */
+    int64_t tiled_fluid;     /* fluid nodes among them */
+    int64_t listed_nodes;    /* length of the node list */
+} lbm_tau1_compact_info;
+
+/* Sets f* (0 <= f <= 1.01; 1.01 sends every non-empty tile column to the
+ * node list, 0 every one to the tiled kernel) and rebuilds the lists now if
+ * the geometry is set (queued on the handle's stream; waits for it). The
+ * state is unchanged. LBM_EINVAL: not the compact layout, f out of range. */
+lbm_status lbm_tau1_set_compact_threshold(lbm_tau1* h, double f);
+
+/* Fills *out. LBM_EINVAL: NULL argument or not the compact layout;
+ * LBM_ESTATE: no geometry yet. */
+lbm_status lbm_tau1_get_compact_info(const lbm_tau1* h, lbm_tau1_compact_info* out);
 
 /* ---- Batches: many boxes stepped together (continuous batching) ----------
  * No counterpart in the paper, which steps one domain at a time. A batch

@@ -6,6 +6,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "host.h"
 #include "kernels.h"
@@ -44,6 +45,17 @@ struct lbm_tau1 {
     int* nbr = nullptr;         // sparse: neighbour table [(q-1)][nf]
     int64_t launches = 0;
     unsigned int* dtimeouts = nullptr;  // device counter of staged-copy waits that ran out
+    bool compact = false;       // compact layout: dense records, work split by tile column
+    double cthr = 0.3;          // compact: fluid fraction from which a tile column is tiled
+    bool c_tiled_ok = false;    // compact: the row-pair kernel takes the box's tile columns
+    int* ccounts = nullptr;     // compact: device fluid count of every tile column
+    std::vector<int> ccounts_host;
+    int* ctiles = nullptr;      // compact: tile columns of the row-pair kernel [columns]
+    int* clisted = nullptr;     // compact: tile columns of the node list, then their offsets [2 columns]
+    int* cnodes = nullptr;      // compact: the node list [fluid nodes]
+    int64_t n_ctiles = 0, n_clisted = 0, n_cnodes = 0, c_tiled_fluid = 0, c_empty = 0;
+    cudaStream_t cside = nullptr;   // compact: the node-list kernel's stream when both kernels run
+    cudaEvent_t cfork = nullptr, cjoin = nullptr;
     int p_axis = -1;            // constant-density faces on this axis (-1: none)
     double p_lo = 1.0, p_hi = 1.0;
     std::string err;
@@ -92,6 +104,13 @@ void free_all(lbm_tau1* h)
     if (h->dscale) cudaFree(h->dscale);
     if (h->rescale_scratch) cudaFree(h->rescale_scratch);
     if (h->dtimeouts) cudaFree(h->dtimeouts);
+    if (h->ccounts) cudaFree(h->ccounts);
+    if (h->ctiles) cudaFree(h->ctiles);
+    if (h->clisted) cudaFree(h->clisted);
+    if (h->cnodes) cudaFree(h->cnodes);
+    if (h->cfork) cudaEventDestroy(h->cfork);
+    if (h->cjoin) cudaEventDestroy(h->cjoin);
+    if (h->cside) cudaStreamDestroy(h->cside);
 }
 
 // Staged-copy waits that ran out since the last call (reads the device
@@ -283,9 +302,105 @@ lbm_status build_fluid_list(lbm_tau1* h)
     return LBM_OK;
 }
 
+// Compact layout: classes the tile columns by their fluid counts (counted
+// once per geometry) with threshold h->cthr and uploads the two lists; the
+// node list is written by a kernel from the flags.
+lbm_status build_compact(lbm_tau1* h)
+{
+    const lbm_tau1_config& c = h->cfg;
+    const int64_t nb = compact_tile_columns(c.q, c.storage, c.nx, c.ny, c.nz);
+    if ((int64_t)h->ccounts_host.size() != nb) {
+        if (!h->ccounts) {
+            LBM_CUDA(h, cudaMalloc((void**)&h->ccounts, (size_t)nb * sizeof(int)), "compact: counts");
+            LBM_CUDA(h, cudaMalloc((void**)&h->ctiles, (size_t)nb * sizeof(int)), "compact: tile list");
+            LBM_CUDA(h, cudaMalloc((void**)&h->clisted, (size_t)2 * nb * sizeof(int)), "compact: listed columns");
+        }
+        LBM_CUDA(h, launch_compact_count(c.q, c.storage, c.nx, c.ny, c.nz, h->flags, h->ccounts, h->stream),
+                 "compact: count kernel");
+        ++h->launches;
+        h->ccounts_host.assign((size_t)nb, 0);
+        LBM_CUDA(h, cudaMemcpyAsync(h->ccounts_host.data(), h->ccounts, (size_t)nb * sizeof(int),
+                                    cudaMemcpyDefault, h->stream), "compact: counts copy");
+        LBM_CUDA(h, cudaStreamSynchronize(h->stream), "compact: counts sync");
+        int64_t nf = 0;
+        for (int v : h->ccounts_host) nf += v;
+        if (h->cnodes) { cudaFree(h->cnodes); h->cnodes = nullptr; }
+        LBM_CUDA(h, cudaMalloc((void**)&h->cnodes, (size_t)(nf > 0 ? nf : 1) * sizeof(int)), "compact: node list");
+        StepArgs a;
+        fill_args(h, a);
+        h->c_tiled_ok = tau1_rowpair_ok(c.q, c.storage, 0, a);
+        if (h->c_tiled_ok && !h->cside) {
+            LBM_CUDA(h, cudaStreamCreateWithFlags(&h->cside, cudaStreamNonBlocking), "compact: side stream");
+            LBM_CUDA(h, cudaEventCreateWithFlags(&h->cfork, cudaEventDisableTiming), "compact: event");
+            LBM_CUDA(h, cudaEventCreateWithFlags(&h->cjoin, cudaEventDisableTiming), "compact: event");
+        }
+    }
+    std::vector<int> tiles, listed, offsets;
+    int64_t nodes = 0;
+    h->c_tiled_fluid = 0;
+    h->c_empty = 0;
+    for (int64_t b = 0; b < nb; ++b) {
+        const int cnt = h->ccounts_host[(size_t)b];
+        if (cnt == 0) { ++h->c_empty; continue; }
+        const double m = (double)compact_tile_nodes(c.q, c.storage, c.nx, c.ny, c.nz, (int)b);
+        if (h->c_tiled_ok && (double)cnt >= h->cthr * m) {
+            tiles.push_back((int)b);
+            h->c_tiled_fluid += cnt;
+        } else {
+            listed.push_back((int)b);
+            offsets.push_back((int)nodes);
+            nodes += cnt;
+        }
+    }
+    listed.insert(listed.end(), offsets.begin(), offsets.end());
+    h->n_ctiles = (int64_t)tiles.size();
+    h->n_clisted = (int64_t)offsets.size();
+    h->n_cnodes = nodes;
+    if (!tiles.empty())
+        LBM_CUDA(h, cudaMemcpyAsync(h->ctiles, tiles.data(), tiles.size() * sizeof(int), cudaMemcpyDefault,
+                                    h->stream), "compact: tile list copy");
+    if (!listed.empty())
+        LBM_CUDA(h, cudaMemcpyAsync(h->clisted, listed.data(), listed.size() * sizeof(int), cudaMemcpyDefault,
+                                    h->stream), "compact: listed columns copy");
+    LBM_CUDA(h, launch_compact_nodes(c.q, c.storage, c.nx, c.ny, c.nz, h->flags, h->clisted,
+                                     h->clisted + h->n_clisted, (int)h->n_clisted, h->cnodes, h->stream),
+             "compact: node list kernel");
+    if (h->n_clisted) ++h->launches;
+    // the host vectors are copied from before they go out of scope
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream), "compact: lists sync");
+    return LBM_OK;
+}
+
+// Kernel launches of one step of the main kernel(s).
+int step_launches(const lbm_tau1* h)
+{
+    if (!h->compact) return 1;
+    return (h->n_ctiles > 0 ? 1 : 0) + (h->n_cnodes > 0 ? 1 : 0);
+}
+
 cudaError_t launch_kernel(const lbm_tau1* h, int variant, const StepArgs& a)
 {
     if (h->cfg.q == LBM_D2Q9) return launch_tau1_2d(h->kernel == LBM_KERNEL_SIMPLE, h->cfg.storage, a, h->stream);
+    if (h->compact) {
+        // Disjoint node sets, both read from the same copy: with both lists
+        // non-empty the node-list kernel runs on a side stream forked from
+        // and joined back into the handle's stream, so that the two kernels
+        // overlap (each fills the SMs the other's tail leaves idle).
+        const bool both = h->n_ctiles > 0 && h->n_cnodes > 0;
+        cudaStream_t ls = both ? h->cside : h->stream;
+        cudaError_t e = cudaSuccess;
+        if (both) {
+            e = cudaEventRecord(h->cfork, h->stream);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(h->cside, h->cfork, 0);
+        }
+        if (e == cudaSuccess) e = launch_tau1_list(h->cfg.q, h->cfg.storage, a, h->cnodes, h->n_cnodes, ls);
+        if (e == cudaSuccess && both) e = cudaEventRecord(h->cjoin, h->cside);
+        if (e == cudaSuccess)
+            e = launch_tau1_rowpair_list(h->cfg.q, h->cfg.storage, COMPACT_ZCHUNK, a, h->ctiles, (int)h->n_ctiles,
+                                         h->stream);
+        if (e == cudaSuccess && both) e = cudaStreamWaitEvent(h->stream, h->cjoin, 0);
+        return e;
+    }
     if (h->sparse) return launch_tau1_sparse(h->cfg.q, h->cfg.storage, a, (int)h->nf, h->nbr, h->stream);
     if (h->kernel == LBM_KERNEL_TILED) return launch_tau1_tiled(h->cfg.q, h->cfg.storage, variant, a, h->stream);
     return launch_tau1_simple(h->cfg.q, h->cfg.storage, a, h->stream);
@@ -306,7 +421,7 @@ lbm_status launch_step(lbm_tau1* h)
     }
     cudaError_t e = launch_kernel(h, h->variant, a);
     if (e != cudaSuccess) return cuda_fail(h, e, "tau1 step launch");
-    ++h->launches;
+    h->launches += step_launches(h);
     if (h->p_axis >= 0) {
         e = launch_zou_he(h->cfg.q, h->cfg.storage, a, h->p_axis, h->p_lo, h->p_hi, h->stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "pressure-face launch");
@@ -321,6 +436,50 @@ lbm_status launch_step(lbm_tau1* h)
         h->launches += 3;
         if (e != cudaSuccess) return cuda_fail(h, e, "rescale kernels");
     }
+    return LBM_OK;
+}
+
+// Compact layout: times every threshold of LBM_TAU1_COMPACT_THRESHOLDS (the
+// trial launches rewrite only the scratch copy) and keeps the fastest.
+lbm_status autotune_compact(lbm_tau1* h, int trials, int32_t* chosen, float* ms_per_step)
+{
+    static const double thr[] = LBM_TAU1_COMPACT_THRESHOLDS;
+    const int nt = (int)(sizeof(thr) / sizeof(thr[0]));
+    StepArgs a;
+    fill_args(h, a);
+    cudaEvent_t e0, e1;
+    LBM_CUDA(h, cudaEventCreate(&e0), "autotune: event");
+    cudaError_t e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) { cudaEventDestroy(e0); return cuda_fail(h, e, "autotune: event"); }
+    int best = 0;
+    float best_ms = 0.f;
+    lbm_status st = LBM_OK;
+    for (int v = 0; v < nt && e == cudaSuccess && st == LBM_OK; ++v) {
+        h->cthr = thr[v];
+        st = build_compact(h);
+        if (st != LBM_OK) break;
+        e = launch_kernel(h, 0, a);
+        h->launches += step_launches(h);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+        for (int t = 0; t < trials && e == cudaSuccess; ++t) {
+            e = launch_kernel(h, 0, a);
+            h->launches += step_launches(h);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        ms /= (float)trials;
+        if (e == cudaSuccess && (v == 0 || ms < best_ms)) { best = v; best_ms = ms; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != LBM_OK) return st;
+    if (e != cudaSuccess) return cuda_fail(h, e, "autotune: trial");
+    h->cthr = thr[best];
+    if (lbm_status s2 = build_compact(h)) return s2;
+    if (chosen) *chosen = best;
+    if (ms_per_step) *ms_per_step = best_ms;
     return LBM_OK;
 }
 
@@ -365,11 +524,12 @@ lbm_status lbm_tau1_create(const lbm_tau1_config* cfg, lbm_tau1** out)
         return fail(nullptr, LBM_EINVAL, "create: D2Q9 takes one plane (nz = 1), the dense layout and the Tau1 scheme");
     if (storage_node_bytes(cfg->storage) == 0) return fail(nullptr, LBM_EINVAL, "create: bad storage");
     if (cfg->nx < 1 || cfg->ny < 1 || cfg->nz < 1) return fail(nullptr, LBM_EINVAL, "create: box sizes must be >= 1");
-    if (cfg->layout != LBM_DENSE && cfg->layout != LBM_SPARSE) return fail(nullptr, LBM_EINVAL, "create: bad layout");
-    if (cfg->layout == LBM_SPARSE && cfg->scheme != LBM_SCHEME_TAU1)
-        return fail(nullptr, LBM_EINVAL, "create: the sparse layout is for the Tau1 scheme");
-    if (cfg->layout == LBM_SPARSE && (int64_t)cfg->nx * cfg->ny * cfg->nz >= ((int64_t)1 << 31))
-        return fail(nullptr, LBM_EINVAL, "create: the sparse layout takes boxes of fewer than 2^31 nodes");
+    if (cfg->layout != LBM_DENSE && cfg->layout != LBM_SPARSE && cfg->layout != LBM_COMPACT)
+        return fail(nullptr, LBM_EINVAL, "create: bad layout");
+    if (cfg->layout != LBM_DENSE && cfg->scheme != LBM_SCHEME_TAU1)
+        return fail(nullptr, LBM_EINVAL, "create: the sparse and compact layouts are for the Tau1 scheme");
+    if (cfg->layout != LBM_DENSE && (int64_t)cfg->nx * cfg->ny * cfg->nz >= ((int64_t)1 << 31))
+        return fail(nullptr, LBM_EINVAL, "create: the sparse and compact layouts take boxes of fewer than 2^31 nodes");
     if (cfg->scheme != LBM_SCHEME_TAU1 && cfg->scheme != LBM_SCHEME_BGK)
         return fail(nullptr, LBM_EINVAL, "create: bad scheme");
     if (cfg->scheme == LBM_SCHEME_BGK && !bgk_supported(cfg->q, cfg->storage))
@@ -388,7 +548,9 @@ lbm_status lbm_tau1_create(const lbm_tau1_config* cfg, lbm_tau1** out)
     h->node_bytes = storage_node_bytes(cfg->storage);
     h->kernel = cfg->kernel;
     h->sparse = cfg->layout == LBM_SPARSE;
-    if (h->sparse) h->kernel = LBM_KERNEL_SIMPLE;  // one thread per fluid node; no tile variants
+    h->compact = cfg->layout == LBM_COMPACT;
+    // one thread per fluid node, or the compact split: no tile variants
+    if (h->sparse || h->compact) h->kernel = LBM_KERNEL_SIMPLE;
     const bool tiled_ok = cfg->q == LBM_D2Q9 || tau1_tiled_supported(cfg->q, cfg->storage, n);
     if (h->kernel == LBM_KERNEL_AUTO) h->kernel = tiled_ok ? LBM_KERNEL_TILED : LBM_KERNEL_SIMPLE;
     if (h->kernel == LBM_KERNEL_TILED && !tiled_ok) {
@@ -398,7 +560,9 @@ lbm_status lbm_tau1_create(const lbm_tau1_config* cfg, lbm_tau1** out)
     cudaError_t e = cudaSuccess;
     h->bgk = cfg->scheme == LBM_SCHEME_BGK;
     // dense: two copies of the box; sparse: allocated by set_geometry (nf records)
-    for (int b = 0; b < 2 && e == cudaSuccess && !h->sparse; ++b) e = cudaMalloc(&h->buf[b], (size_t)n * h->node_bytes);
+    // (compact: one more record, the solid sentinel of the node-list kernel)
+    for (int b = 0; b < 2 && e == cudaSuccess && !h->sparse; ++b)
+        e = cudaMalloc(&h->buf[b], (size_t)(n + (h->compact ? 1 : 0)) * h->node_bytes);
     if (h->bgk)
         for (int b = 0; b < 2 && e == cudaSuccess; ++b)
             e = cudaMalloc(&h->fbuf[b], (size_t)n * cfg->q * (cfg->storage == LBM_F64 ? 8 : 4));
@@ -458,6 +622,10 @@ lbm_status lbm_tau1_set_geometry(lbm_tau1* h, const uint8_t* solid, int on_devic
     if (e != cudaSuccess) return cuda_fail(h, e, "set_geometry: flags kernel");
     if (h->sparse)
         if (lbm_status st = build_fluid_list(h)) return st;
+    if (h->compact) {
+        h->ccounts_host.clear();  // a new geometry: count again
+        if (lbm_status st = build_compact(h)) return st;
+    }
     const double zero[4] = {0, 0, 0, 0};
     set_scales(h, zero);
     if (lbm_status st = upload_scales(h)) return st;
@@ -466,6 +634,10 @@ lbm_status lbm_tau1_set_geometry(lbm_tau1* h, const uint8_t* solid, int on_devic
         if (h->sparse) e = launch_import_sparse(h->cfg.storage, (int)h->nf, nullptr, h->pos, h->buf[b], h->scale, h->stream);
         else e = launch_import_state(h->cfg.storage, h->n, nullptr, h->buf[b], h->flags, h->scale, h->stream);
         ++h->launches;
+        if (e == cudaSuccess && h->compact) {
+            e = launch_compact_sentinel(h->cfg.storage, h->buf[b], h->n, h->dscale, h->stream);
+            ++h->launches;
+        }
         if (e != cudaSuccess) return cuda_fail(h, e, "set_geometry: state init");
     }
     h->cur = 0;
@@ -642,6 +814,45 @@ lbm_status lbm_tau1_set_variant(lbm_tau1* h, int32_t variant)
     return LBM_OK;
 }
 
+lbm_status lbm_tau1_set_compact_threshold(lbm_tau1* h, double f)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "set_compact_threshold: NULL handle");
+    if (!h->compact) return fail(h, LBM_EINVAL, "set_compact_threshold: not the compact layout");
+    if (!(f >= 0.0 && f <= 1.01)) return fail(h, LBM_EINVAL, "set_compact_threshold: f outside [0, 1.01]");
+    h->cthr = f;
+    return h->has_geometry ? build_compact(h) : LBM_OK;
+}
+
+lbm_status lbm_tau1_get_compact_info(const lbm_tau1* h, lbm_tau1_compact_info* out)
+{
+    if (!h || !out) return fail(const_cast<lbm_tau1*>(h), LBM_EINVAL, "get_compact_info: NULL argument");
+    lbm_tau1* hm = const_cast<lbm_tau1*>(h);
+    if (!h->compact) return fail(hm, LBM_EINVAL, "get_compact_info: not the compact layout");
+    if (!h->has_geometry) return fail(hm, LBM_ESTATE, "get_compact_info: call set_geometry first");
+    const lbm_tau1_config& c = h->cfg;
+    std::memset(out, 0, sizeof(*out));
+    out->threshold = h->cthr;
+    out->tile[0] = 32;
+    out->tile[1] = tau1_rowpair_tile_height(c.q, c.storage, 0);
+    out->tile[2] = c.nz < COMPACT_ZCHUNK ? c.nz : COMPACT_ZCHUNK;
+    out->tiled_ok = h->c_tiled_ok ? 1 : 0;
+    out->columns = (int64_t)h->ccounts_host.size();
+    out->empty_columns = h->c_empty;
+    out->tiled_columns = h->n_ctiles;
+    out->listed_columns = h->n_clisted;
+    int64_t tn = 0;
+    for (size_t b = 0; b < h->ccounts_host.size(); ++b) {
+        const int cnt = h->ccounts_host[b];
+        const int64_t m = compact_tile_nodes(c.q, c.storage, c.nx, c.ny, c.nz, (int)b);
+        if (cnt == m) ++out->full_columns;
+        if (h->c_tiled_ok && cnt > 0 && (double)cnt >= h->cthr * (double)m) tn += m;
+    }
+    out->tiled_nodes = tn;
+    out->tiled_fluid = h->c_tiled_fluid;
+    out->listed_nodes = h->n_cnodes;
+    return LBM_OK;
+}
+
 lbm_status lbm_tau1_autotune(lbm_tau1* h, int32_t trials, int32_t* chosen, float* ms_per_step)
 {
     if (!h) return fail(nullptr, LBM_EINVAL, "autotune: NULL handle");
@@ -652,6 +863,7 @@ lbm_status lbm_tau1_autotune(lbm_tau1* h, int32_t trials, int32_t* chosen, float
         if (ms_per_step) *ms_per_step = 0.f;
         return LBM_OK;
     }
+    if (h->compact) return autotune_compact(h, trials, chosen, ms_per_step);
     const std::string key = tune_key(h);
     int cached = 0;
     double cached_ms = 0;

@@ -26,6 +26,29 @@ cudaError_t encode_state_map(int storage, const void* base, int nx, int ny, int 
 int tau1_rowpair_shapes(int storage);
 bool tau1_rowpair_ok(int q, int storage, int shape, const StepArgs& a);
 cudaError_t launch_tau1_rowpair(int q, int storage, int shape, int zchunk, const StepArgs& a, cudaStream_t s);
+// Tile height (2W) of a row-pair shape (0 if none), and the row-pair kernel of
+// shape 0 over a list of tile columns (indices b of the grid order: tile
+// b % ntiles, z chunk b / ntiles, ntiles = (nx / 32) (ny / tile height)).
+int tau1_rowpair_tile_height(int q, int storage, int shape);
+cudaError_t launch_tau1_rowpair_list(int q, int storage, int zchunk, const StepArgs& a, const int* list, int count,
+                                     cudaStream_t s);
+// Compact porous layout (compact.cu): tile columns of 32 x H x COMPACT_ZCHUNK
+// nodes (H the row-pair tile height of shape 0), numbered like the row-pair
+// grid; fluid counts per tile column, and the fluid nodes of listed tile
+// columns in row order at the given offsets.
+constexpr int COMPACT_ZCHUNK = 24;
+int64_t compact_tile_columns(int q, int storage, int nx, int ny, int nz);
+int64_t compact_tile_nodes(int q, int storage, int nx, int ny, int nz, int b);
+cudaError_t launch_compact_count(int q, int storage, int nx, int ny, int nz, const uint8_t* flags, int* counts,
+                                 cudaStream_t s);
+cudaError_t launch_compact_nodes(int q, int storage, int nx, int ny, int nz, const uint8_t* flags, const int* tiles,
+                                 const int* offsets, int ntiles, int* nodes, cudaStream_t s);
+// Tau1 step of the listed box nodes (fluid), one thread per node, the
+// neighbours gathered from the dense records (the dense kernels' values); the
+// state copies hold n + 1 records, record n the solid sentinel written by
+// launch_compact_sentinel (dscale: the 16-bit scales, or NULL).
+cudaError_t launch_compact_sentinel(int storage, void* buf, int64_t n, const float* dscale, cudaStream_t s);
+cudaError_t launch_tau1_list(int q, int storage, const StepArgs& a, const int* nodes, int64_t count, cudaStream_t s);
 
 // D2Q9 (one plane): simple = one thread per node, else the y-marching warp
 // kernel; same bits.

@@ -16,13 +16,16 @@ using namespace rp;
 
 template <int Q, int ST, int W, int MINB>
 __global__ void __launch_bounds__(32 * W, MINB)
-    tau1_rowpair_kernel(StepArgs a, int ntx, int ntiles, int chunk, const __grid_constant__ CUtensorMap tmap)
+    tau1_rowpair_kernel(StepArgs a, int ntx, int ntiles, int chunk, const __grid_constant__ CUtensorMap tmap,
+                        const int* __restrict__ list)
 {
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     // stage buffers of the tensor copies want 128-byte alignment
     unsigned char* smem = smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u);
-    const int tile = blockIdx.x % ntiles;
-    const int z0 = (blockIdx.x / ntiles) * chunk;
+    // the tile columns of the whole box in grid order, or those of a list
+    const int b = list ? list[blockIdx.x] : (int)blockIdx.x;
+    const int tile = b % ntiles;
+    const int z0 = (b / ntiles) * chunk;
     const int z1 = min(a.nz, z0 + chunk);
     const int x0 = (tile % ntx) * 32, y0 = (tile / ntx) * (2 * W);
     const Scales sc(a.dscale);
@@ -34,7 +37,7 @@ __global__ void __launch_bounds__(32 * W, MINB)
 }
 
 template <int Q, int ST, int V>
-cudaError_t launch_t(const StepArgs& a, int zchunk, cudaStream_t s)
+cudaError_t launch_t(const StepArgs& a, int zchunk, cudaStream_t s, const int* list = nullptr, int count = 0)
 {
     using E = typename Storage<ST>::ctype;
     constexpr int W = RShape<Q, E, V>::W;
@@ -51,9 +54,10 @@ cudaError_t launch_t(const StepArgs& a, int zchunk, cudaStream_t s)
     const int ntiles = ntx * (a.ny / (2 * W));
     const int chunk = a.nz < zchunk ? a.nz : zchunk;
     const int nchunks = (a.nz + chunk - 1) / chunk;
-    const long long blocks = (long long)ntiles * nchunks;
+    const long long blocks = list ? (long long)count : (long long)ntiles * nchunks;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    kern<<<(unsigned)blocks, 32 * W, SMEM, s>>>(a, ntx, ntiles, chunk, map);
+    if (blocks == 0) return cudaSuccess;
+    kern<<<(unsigned)blocks, 32 * W, SMEM, s>>>(a, ntx, ntiles, chunk, map, list);
     return cudaGetLastError();
 }
 
@@ -97,6 +101,24 @@ bool tau1_rowpair_ok(int q, int storage, int shape, const StepArgs& a)
     if ((reinterpret_cast<uintptr_t>(a.pre) & 15) != 0) return false;
     CUtensorMap probe;
     return encode_state_map(storage, a.pre, a.nx, a.ny, a.nz, 2 * w + 2, &probe) == cudaSuccess;
+}
+
+int tau1_rowpair_tile_height(int q, int storage, int shape) { return 2 * shape_w(q, storage, shape); }
+
+cudaError_t launch_tau1_rowpair_list(int q, int storage, int zchunk, const StepArgs& a, const int* list, int count,
+                                     cudaStream_t s)
+{
+    switch (q * 10 + storage) {
+    case 190 + ST_F64: return launch_t<19, ST_F64, 0>(a, zchunk, s, list, count);
+    case 190 + ST_F32: return launch_t<19, ST_F32, 0>(a, zchunk, s, list, count);
+    case 190 + ST_F16S: return launch_t<19, ST_F16S, 0>(a, zchunk, s, list, count);
+    case 190 + ST_BF16S: return launch_t<19, ST_BF16S, 0>(a, zchunk, s, list, count);
+    case 270 + ST_F64: return launch_t<27, ST_F64, 0>(a, zchunk, s, list, count);
+    case 270 + ST_F32: return launch_t<27, ST_F32, 0>(a, zchunk, s, list, count);
+    case 270 + ST_F16S: return launch_t<27, ST_F16S, 0>(a, zchunk, s, list, count);
+    case 270 + ST_BF16S: return launch_t<27, ST_BF16S, 0>(a, zchunk, s, list, count);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_tau1_rowpair(int q, int storage, int shape, int zchunk, const StepArgs& a, cudaStream_t s)

@@ -23,7 +23,10 @@ STATUS_NAMES = ["LBM_OK", "LBM_EINVAL", "LBM_ENOMEM", "LBM_ECUDA", "LBM_EDIVERGE
 LBM_D2Q9, LBM_D3Q19, LBM_D3Q27 = 9, 19, 27
 LBM_F64, LBM_F32, LBM_F16S, LBM_BF16S = range(4)
 STORAGE = {"f64": LBM_F64, "f32": LBM_F32, "f16s": LBM_F16S, "bf16s": LBM_BF16S}
-LBM_DENSE, LBM_SPARSE = 0, 1
+LBM_DENSE, LBM_SPARSE, LBM_COMPACT = 0, 1, 2
+LAYOUTS = {"dense": LBM_DENSE, "sparse": LBM_SPARSE, "compact": LBM_COMPACT}
+# thresholds f* that lbm_tau1_autotune times for the compact layout (the header's list)
+COMPACT_THRESHOLDS = (0.0, 0.1, 0.2, 0.3, 0.4, 0.5, 0.7, 1.01)
 LBM_SCHEME_TAU1, LBM_SCHEME_BGK = 0, 1
 LBM_KERNEL_AUTO, LBM_KERNEL_SIMPLE, LBM_KERNEL_TILED = 0, 1, 2
 KERNELS = {"auto": LBM_KERNEL_AUTO, "simple": LBM_KERNEL_SIMPLE, "tiled": LBM_KERNEL_TILED}
@@ -47,6 +50,19 @@ class lbm_tau1_stats(ctypes.Structure):
                 "mass": self.mass, "drho_sum": self.drho_sum, "mean_ux_superficial": self.mean_ux_superficial,
                 "mean_u_fluid": tuple(self.mean_u_fluid), "max_abs_u": self.max_abs_u,
                 "permeability": self.permeability}
+
+
+class lbm_tau1_compact_info(ctypes.Structure):
+    _fields_ = [("threshold", ctypes.c_double), ("tile", ctypes.c_int32 * 3), ("tiled_ok", ctypes.c_int32),
+                ("columns", ctypes.c_int64), ("empty_columns", ctypes.c_int64), ("full_columns", ctypes.c_int64),
+                ("tiled_columns", ctypes.c_int64),
+                ("listed_columns", ctypes.c_int64), ("tiled_nodes", ctypes.c_int64), ("tiled_fluid", ctypes.c_int64),
+                ("listed_nodes", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["tile"] = tuple(self.tile)
+        return d
 
 
 class lbm_tau1_batch_config(ctypes.Structure):
@@ -75,6 +91,8 @@ SIGNATURES = {
     "lbm_tau1_launch_count": (_I64, [_H]),
     "lbm_tau1_set_pressure": (_I, [_H, ctypes.c_int32, ctypes.c_double, ctypes.c_double]),
     "lbm_tau1_copy_plane": (_I, [_H, ctypes.c_int32, _P, ctypes.c_int32]),
+    "lbm_tau1_set_compact_threshold": (_I, [_H, ctypes.c_double]),
+    "lbm_tau1_get_compact_info": (_I, [_H, ctypes.POINTER(lbm_tau1_compact_info)]),
     "lbm_tau1_variant_count": (ctypes.c_int32, [_H]),
     "lbm_tau1_set_variant": (_I, [_H, ctypes.c_int32]),
     "lbm_tau1_autotune": (_I, [_H, ctypes.c_int32, _P, _P]),
@@ -184,6 +202,14 @@ def lbm_tau1_copy_plane(h, z: int, buf, to_handle: int) -> int:
     return _fn("lbm_tau1_copy_plane")(h, z, buf, to_handle)
 
 
+def lbm_tau1_set_compact_threshold(h, f: float) -> int:
+    return _fn("lbm_tau1_set_compact_threshold")(h, f)
+
+
+def lbm_tau1_get_compact_info(h, out: lbm_tau1_compact_info) -> int:
+    return _fn("lbm_tau1_get_compact_info")(h, ctypes.byref(out))
+
+
 def lbm_tau1_variant_count(h) -> int:
     return _fn("lbm_tau1_variant_count")(h)
 
@@ -287,7 +313,7 @@ class Tau1:
                  kernel: str = "auto", stream=None, scheme: int = LBM_SCHEME_TAU1, layout=LBM_DENSE):
         nx, ny, nz = (int(d) for d in dims)
         if isinstance(layout, str):
-            layout = {"dense": LBM_DENSE, "sparse": LBM_SPARSE}[layout]
+            layout = LAYOUTS[layout]
         cfg = lbm_tau1_config()
         cfg.q, cfg.storage, cfg.layout, cfg.scheme = int(q), STORAGE[storage], int(layout), int(scheme)
         cfg.nx, cfg.ny, cfg.nz = nx, ny, nz
@@ -348,6 +374,17 @@ class Tau1:
         """Constant-density (Zou-He) faces on a non-periodic axis (-1: none)."""
         self._check(lbm_tau1_set_pressure(self.h, int(axis), float(rho_lo), float(rho_hi)))
 
+    def set_compact_threshold(self, f: float) -> None:
+        """Compact layout: fluid fraction f* from which a tile column goes to
+        the tiled kernel (the lists are rebuilt; the state is unchanged)."""
+        self._check(lbm_tau1_set_compact_threshold(self.h, float(f)))
+
+    def compact_info(self) -> dict:
+        """Compact layout: how the box is split (tile columns per class, nodes)."""
+        s = lbm_tau1_compact_info()
+        self._check(lbm_tau1_get_compact_info(self.h, s))
+        return s.as_dict()
+
     def reduce(self, allow_diverged: bool = False) -> dict:
         s = lbm_tau1_stats()
         st = lbm_tau1_reduce(self.h, s)
@@ -362,7 +399,8 @@ class Tau1:
         self._check(lbm_tau1_synchronize(self.h))
 
     def autotune(self, trials: int = 20) -> tuple[int, float]:
-        """Times each tile-shape variant; keeps the fastest. Returns (variant, ms per step)."""
+        """Times each tile-shape variant (compact layout: each threshold of
+        COMPACT_THRESHOLDS); keeps the fastest. Returns (index, ms per step)."""
         ch = ctypes.c_int32(0)
         ms = ctypes.c_float(0)
         self._check(lbm_tau1_autotune(self.h, int(trials), ctypes.byref(ch), ctypes.byref(ms)))
