@@ -71,7 +71,9 @@ typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16S = 2, LBM_BF16S = 3 } lbm_stora
  * sparse layout is for the Tau1 scheme, boxes of fewer than 2^31 nodes; its
  * FP32 and FP64 results equal the dense kernels' bits. */
 /* COMPACT: the dense records, with each step's work split by tile column
- * (32 x H x 24 nodes, H the tiled kernel's tile height): tile columns without
+ * (32 x H x 24 or 32 nodes: the tile column of the row-pair variant chosen
+ * with lbm_tau1_set_variant, 2R variants as for the dense layout's row-pair
+ * kernel, variant 0 by default): tile columns without
  * fluid are never read or written; those whose fluid fraction is at least the
  * threshold f* are stepped by the tiled kernel through a list; the fluid
  * nodes of the others are stepped one thread per node through a 4-byte list
@@ -226,7 +228,9 @@ lbm_status lbm_tau1_copy_plane(lbm_tau1* h, int32_t z, void* buf, int32_t to_han
 /* Number of variants of the handle's step kernel (1 if it has none). */
 int32_t lbm_tau1_variant_count(const lbm_tau1* h);
 
-/* Selects a variant, 0 <= variant < lbm_tau1_variant_count(h). LBM_EINVAL otherwise. */
+/* Selects a variant, 0 <= variant < lbm_tau1_variant_count(h). LBM_EINVAL otherwise.
+ * Compact layout: the lists are rebuilt now if the geometry is set (waits for
+ * the stream); the state is unchanged. */
 lbm_status lbm_tau1_set_variant(lbm_tau1* h, int32_t variant);
 
 /* Times every variant for `trials` step launches on the handle's current
@@ -234,10 +238,11 @@ lbm_status lbm_tau1_set_variant(lbm_tau1* h, int32_t variant);
  * and returns its index in *chosen and its time per step in *ms_per_step
  * (either may be NULL). The trial launches rewrite only the scratch copy, so
  * the state and step counter are unchanged. Synchronises the stream.
- * Compact layout: times the thresholds f* of LBM_TAU1_COMPACT_THRESHOLDS
- * instead, rebuilding the lists for each, keeps the fastest and returns its
- * index in that list; the cache is not used (the best f* depends on the
- * medium).
+ * Compact layout: times every pair of a row-pair variant and a threshold f*
+ * of LBM_TAU1_COMPACT_THRESHOLDS (rebuilding the lists for each), keeps the
+ * fastest pair and returns the threshold's index in that list (the variant
+ * is in lbm_tau1_get_compact_info); the cache is not used (the best pair
+ * depends on the medium).
  * Errors: LBM_EINVAL (trials < 1), LBM_ESTATE (no geometry), LBM_ECUDA. */
 #define LBM_TAU1_COMPACT_THRESHOLDS {0.0, 0.1, 0.2, 0.3, 0.4, 0.5, 0.7, 1.01}
 lbm_status lbm_tau1_autotune(lbm_tau1* h, int32_t trials, int32_t* chosen, float* ms_per_step);
@@ -254,7 +259,8 @@ void lbm_tau1_set_tune_cache(const char* path);
 /* Compact layout (LBM_COMPACT): how set_geometry split the box. */
 typedef struct lbm_tau1_compact_info {
     double threshold;        /* f*: fluid fraction from which a tile column is tiled */
-    int32_t tile[3];         /* tile column: 32, H, z chunk (24, or nz if smaller) */
+    int32_t variant;         /* row-pair variant of the tiled kernel (lbm_tau1_set_variant) */
+    int32_t tile[3];         /* tile column: 32, H, z chunk (24 or 32, or nz if smaller) */
     int32_t tiled_ok;        /* 1 if the tiled kernel can take tile columns */
     int64_t columns;         /* tile columns of the box */
     int64_t empty_columns;   /* without a fluid node: never visited */

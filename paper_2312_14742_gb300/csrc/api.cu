@@ -48,6 +48,9 @@ struct lbm_tau1 {
     bool compact = false;       // compact layout: dense records, work split by tile column
     double cthr = 0.3;          // compact: fluid fraction from which a tile column is tiled
     bool c_tiled_ok = false;    // compact: the row-pair kernel takes the box's tile columns
+    CompactTiles ctile{};       // compact: tile columns of the row-pair variant h->variant
+    int ccounted = -1;          // compact: variant whose columns ccounts holds (-1: none)
+    int64_t ccap = 0;           // compact: tile columns the three arrays below can hold
     int* ccounts = nullptr;     // compact: device fluid count of every tile column
     std::vector<int> ccounts_host;
     int* ctiles = nullptr;      // compact: tile columns of the row-pair kernel [columns]
@@ -160,6 +163,7 @@ void fill_args(const lbm_tau1* h, StepArgs& a)
 int variant_count(const lbm_tau1* h)
 {
     if (h->cfg.q == LBM_D2Q9) return 1;
+    if (h->compact) return 2 * tau1_rowpair_shapes(h->cfg.storage);
     return (!h->bgk && h->kernel == LBM_KERNEL_TILED) ? tau1_tiled_variants(h->cfg.q, h->cfg.storage) : 1;
 }
 
@@ -302,38 +306,48 @@ lbm_status build_fluid_list(lbm_tau1* h)
     return LBM_OK;
 }
 
-// Compact layout: classes the tile columns by their fluid counts (counted
-// once per geometry) with threshold h->cthr and uploads the two lists; the
-// node list is written by a kernel from the flags.
+// Compact layout: classes the tile columns of the row-pair variant
+// h->variant by their fluid counts (counted once per geometry and variant)
+// with threshold h->cthr and uploads the two lists; the node list is written
+// by a kernel from the flags.
 lbm_status build_compact(lbm_tau1* h)
 {
     const lbm_tau1_config& c = h->cfg;
-    const int64_t nb = compact_tile_columns(c.q, c.storage, c.nx, c.ny, c.nz);
-    if ((int64_t)h->ccounts_host.size() != nb) {
-        if (!h->ccounts) {
+    h->ctile = compact_tiles(c.q, c.storage, h->variant);
+    const CompactTiles& ct = h->ctile;
+    const int64_t nb = compact_tile_columns(ct, c.nx, c.ny, c.nz);
+    if (h->ccounted != h->variant) {
+        if (nb > h->ccap) {
+            for (int** p : {&h->ccounts, &h->ctiles, &h->clisted})
+                if (*p) { cudaFree(*p); *p = nullptr; }
+            h->ccap = 0;
             LBM_CUDA(h, cudaMalloc((void**)&h->ccounts, (size_t)nb * sizeof(int)), "compact: counts");
             LBM_CUDA(h, cudaMalloc((void**)&h->ctiles, (size_t)nb * sizeof(int)), "compact: tile list");
             LBM_CUDA(h, cudaMalloc((void**)&h->clisted, (size_t)2 * nb * sizeof(int)), "compact: listed columns");
+            h->ccap = nb;
         }
-        LBM_CUDA(h, launch_compact_count(c.q, c.storage, c.nx, c.ny, c.nz, h->flags, h->ccounts, h->stream),
+        LBM_CUDA(h, launch_compact_count(ct, c.nx, c.ny, c.nz, h->flags, h->ccounts, h->stream),
                  "compact: count kernel");
         ++h->launches;
         h->ccounts_host.assign((size_t)nb, 0);
         LBM_CUDA(h, cudaMemcpyAsync(h->ccounts_host.data(), h->ccounts, (size_t)nb * sizeof(int),
                                     cudaMemcpyDefault, h->stream), "compact: counts copy");
         LBM_CUDA(h, cudaStreamSynchronize(h->stream), "compact: counts sync");
-        int64_t nf = 0;
-        for (int v : h->ccounts_host) nf += v;
-        if (h->cnodes) { cudaFree(h->cnodes); h->cnodes = nullptr; }
-        LBM_CUDA(h, cudaMalloc((void**)&h->cnodes, (size_t)(nf > 0 ? nf : 1) * sizeof(int)), "compact: node list");
+        if (!h->cnodes) {  // the fluid nodes of the geometry: the longest node list
+            int64_t nf = 0;
+            for (int v : h->ccounts_host) nf += v;
+            LBM_CUDA(h, cudaMalloc((void**)&h->cnodes, (size_t)(nf > 0 ? nf : 1) * sizeof(int)),
+                     "compact: node list");
+        }
         StepArgs a;
         fill_args(h, a);
-        h->c_tiled_ok = tau1_rowpair_ok(c.q, c.storage, 0, a);
+        h->c_tiled_ok = tau1_rowpair_ok(c.q, c.storage, ct.shape, a);
         if (h->c_tiled_ok && !h->cside) {
             LBM_CUDA(h, cudaStreamCreateWithFlags(&h->cside, cudaStreamNonBlocking), "compact: side stream");
             LBM_CUDA(h, cudaEventCreateWithFlags(&h->cfork, cudaEventDisableTiming), "compact: event");
             LBM_CUDA(h, cudaEventCreateWithFlags(&h->cjoin, cudaEventDisableTiming), "compact: event");
         }
+        h->ccounted = h->variant;
     }
     std::vector<int> tiles, listed, offsets;
     int64_t nodes = 0;
@@ -342,7 +356,7 @@ lbm_status build_compact(lbm_tau1* h)
     for (int64_t b = 0; b < nb; ++b) {
         const int cnt = h->ccounts_host[(size_t)b];
         if (cnt == 0) { ++h->c_empty; continue; }
-        const double m = (double)compact_tile_nodes(c.q, c.storage, c.nx, c.ny, c.nz, (int)b);
+        const double m = (double)compact_tile_nodes(ct, c.nx, c.ny, c.nz, (int)b);
         if (h->c_tiled_ok && (double)cnt >= h->cthr * m) {
             tiles.push_back((int)b);
             h->c_tiled_fluid += cnt;
@@ -362,8 +376,8 @@ lbm_status build_compact(lbm_tau1* h)
     if (!listed.empty())
         LBM_CUDA(h, cudaMemcpyAsync(h->clisted, listed.data(), listed.size() * sizeof(int), cudaMemcpyDefault,
                                     h->stream), "compact: listed columns copy");
-    LBM_CUDA(h, launch_compact_nodes(c.q, c.storage, c.nx, c.ny, c.nz, h->flags, h->clisted,
-                                     h->clisted + h->n_clisted, (int)h->n_clisted, h->cnodes, h->stream),
+    LBM_CUDA(h, launch_compact_nodes(ct, c.nx, c.ny, c.nz, h->flags, h->clisted, h->clisted + h->n_clisted,
+                                     (int)h->n_clisted, h->cnodes, h->stream),
              "compact: node list kernel");
     if (h->n_clisted) ++h->launches;
     // the host vectors are copied from before they go out of scope
@@ -396,8 +410,8 @@ cudaError_t launch_kernel(const lbm_tau1* h, int variant, const StepArgs& a)
         if (e == cudaSuccess) e = launch_tau1_list(h->cfg.q, h->cfg.storage, a, h->cnodes, h->n_cnodes, ls);
         if (e == cudaSuccess && both) e = cudaEventRecord(h->cjoin, h->cside);
         if (e == cudaSuccess)
-            e = launch_tau1_rowpair_list(h->cfg.q, h->cfg.storage, COMPACT_ZCHUNK, a, h->ctiles, (int)h->n_ctiles,
-                                         h->stream);
+            e = launch_tau1_rowpair_list(h->cfg.q, h->cfg.storage, h->ctile.shape, h->ctile.zchunk, a, h->ctiles,
+                                         (int)h->n_ctiles, h->stream);
         if (e == cudaSuccess && both) e = cudaStreamWaitEvent(h->stream, h->cjoin, 0);
         return e;
     }
@@ -439,46 +453,61 @@ lbm_status launch_step(lbm_tau1* h)
     return LBM_OK;
 }
 
-// Compact layout: times every threshold of LBM_TAU1_COMPACT_THRESHOLDS (the
-// trial launches rewrite only the scratch copy) and keeps the fastest.
+// Compact layout: mean time of `trials` step launches (after one warm-up)
+// of the current lists; the launches rewrite only the scratch copy.
+lbm_status time_compact(lbm_tau1* h, int trials, cudaEvent_t e0, cudaEvent_t e1, float* ms)
+{
+    StepArgs a;
+    fill_args(h, a);
+    cudaError_t e = launch_kernel(h, 0, a);
+    h->launches += step_launches(h);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+    for (int t = 0; t < trials && e == cudaSuccess; ++t) {
+        e = launch_kernel(h, 0, a);
+        h->launches += step_launches(h);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+    if (e != cudaSuccess) return cuda_fail(h, e, "autotune: trial");
+    *ms /= (float)trials;
+    return LBM_OK;
+}
+
+// Compact layout: times every pair of a row-pair variant and a threshold of
+// LBM_TAU1_COMPACT_THRESHOLDS and keeps the fastest pair.
 lbm_status autotune_compact(lbm_tau1* h, int trials, int32_t* chosen, float* ms_per_step)
 {
     static const double thr[] = LBM_TAU1_COMPACT_THRESHOLDS;
     const int nt = (int)(sizeof(thr) / sizeof(thr[0]));
-    StepArgs a;
-    fill_args(h, a);
     cudaEvent_t e0, e1;
     LBM_CUDA(h, cudaEventCreate(&e0), "autotune: event");
     cudaError_t e = cudaEventCreate(&e1);
     if (e != cudaSuccess) { cudaEventDestroy(e0); return cuda_fail(h, e, "autotune: event"); }
-    int best = 0;
-    float best_ms = 0.f;
     lbm_status st = LBM_OK;
-    for (int v = 0; v < nt && e == cudaSuccess && st == LBM_OK; ++v) {
-        h->cthr = thr[v];
-        st = build_compact(h);
-        if (st != LBM_OK) break;
-        e = launch_kernel(h, 0, a);
-        h->launches += step_launches(h);
-        if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
-        for (int t = 0; t < trials && e == cudaSuccess; ++t) {
-            e = launch_kernel(h, 0, a);
-            h->launches += step_launches(h);
+    int best_v = h->variant, best_t = 0;
+    float best_ms = -1.f;
+    for (int v = 0; v < variant_count(h) && st == LBM_OK; ++v) {
+        for (int t = 0; t < nt && st == LBM_OK; ++t) {
+            h->variant = v;
+            h->cthr = thr[t];
+            float ms = 0.f;
+            st = build_compact(h);
+            if (st == LBM_OK) st = time_compact(h, trials, e0, e1, &ms);
+            if (st == LBM_OK && (best_ms < 0.f || ms < best_ms)) {
+                best_v = v;
+                best_t = t;
+                best_ms = ms;
+            }
         }
-        if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
-        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-        float ms = 0.f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-        ms /= (float)trials;
-        if (e == cudaSuccess && (v == 0 || ms < best_ms)) { best = v; best_ms = ms; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != LBM_OK) return st;
-    if (e != cudaSuccess) return cuda_fail(h, e, "autotune: trial");
-    h->cthr = thr[best];
+    h->variant = best_v;
+    h->cthr = thr[best_t];
     if (lbm_status s2 = build_compact(h)) return s2;
-    if (chosen) *chosen = best;
+    if (chosen) *chosen = best_t;
     if (ms_per_step) *ms_per_step = best_ms;
     return LBM_OK;
 }
@@ -623,7 +652,9 @@ lbm_status lbm_tau1_set_geometry(lbm_tau1* h, const uint8_t* solid, int on_devic
     if (h->sparse)
         if (lbm_status st = build_fluid_list(h)) return st;
     if (h->compact) {
-        h->ccounts_host.clear();  // a new geometry: count again
+        // a new geometry: count again, and size the node list again
+        h->ccounted = -1;
+        if (h->cnodes) { cudaFree(h->cnodes); h->cnodes = nullptr; }
         if (lbm_status st = build_compact(h)) return st;
     }
     const double zero[4] = {0, 0, 0, 0};
@@ -811,7 +842,7 @@ lbm_status lbm_tau1_set_variant(lbm_tau1* h, int32_t variant)
     if (!h) return fail(nullptr, LBM_EINVAL, "set_variant: NULL handle");
     if (variant < 0 || variant >= variant_count(h)) return fail(h, LBM_EINVAL, "set_variant: no such variant");
     h->variant = variant;
-    return LBM_OK;
+    return (h->compact && h->has_geometry) ? build_compact(h) : LBM_OK;
 }
 
 lbm_status lbm_tau1_set_compact_threshold(lbm_tau1* h, double f)
@@ -832,9 +863,10 @@ lbm_status lbm_tau1_get_compact_info(const lbm_tau1* h, lbm_tau1_compact_info* o
     const lbm_tau1_config& c = h->cfg;
     std::memset(out, 0, sizeof(*out));
     out->threshold = h->cthr;
+    out->variant = h->variant;
     out->tile[0] = 32;
-    out->tile[1] = tau1_rowpair_tile_height(c.q, c.storage, 0);
-    out->tile[2] = c.nz < COMPACT_ZCHUNK ? c.nz : COMPACT_ZCHUNK;
+    out->tile[1] = h->ctile.h;
+    out->tile[2] = c.nz < h->ctile.zchunk ? c.nz : h->ctile.zchunk;
     out->tiled_ok = h->c_tiled_ok ? 1 : 0;
     out->columns = (int64_t)h->ccounts_host.size();
     out->empty_columns = h->c_empty;
@@ -843,7 +875,7 @@ lbm_status lbm_tau1_get_compact_info(const lbm_tau1* h, lbm_tau1_compact_info* o
     int64_t tn = 0;
     for (size_t b = 0; b < h->ccounts_host.size(); ++b) {
         const int cnt = h->ccounts_host[b];
-        const int64_t m = compact_tile_nodes(c.q, c.storage, c.nx, c.ny, c.nz, (int)b);
+        const int64_t m = compact_tile_nodes(h->ctile, c.nx, c.ny, c.nz, (int)b);
         if (cnt == m) ++out->full_columns;
         if (h->c_tiled_ok && cnt > 0 && (double)cnt >= h->cthr * (double)m) tn += m;
     }

@@ -1,6 +1,6 @@
 // Compact porous layout: the dense state records, with the work of a step
-// split by tile column (a 32 x H tile of the x-y plane, a chunk of z planes;
-// the row-pair kernel's unit of work).
+// split by tile column (a 32 x H tile of the x-y plane, a chunk of 24 or 32
+// z planes: the unit of work of one row-pair kernel variant).
 //
 // The paper's kernels skip solid chunks and treat mixed chunks through the
 // node mask (Section 3.2); its bandwidth model for porous media charges a
@@ -219,14 +219,14 @@ __global__ void __launch_bounds__(CT) tile_nodes_kernel(TileGeo g, const uint8_t
     }
 }
 
-TileGeo geo_of(int q, int storage, int nx, int ny, int nz)
+TileGeo geo_of(const CompactTiles& t, int nx, int ny, int nz)
 {
     TileGeo g;
     g.nx = nx;
     g.ny = ny;
     g.nz = nz;
-    g.h = tau1_rowpair_tile_height(q, storage, 0);
-    g.chunk = nz < COMPACT_ZCHUNK ? nz : COMPACT_ZCHUNK;
+    g.h = t.h;
+    g.chunk = nz < t.zchunk ? nz : t.zchunk;
     g.ntx = (nx + 31) / 32;
     g.ntiles = g.ntx * ((ny + g.h - 1) / g.h);
     return g;
@@ -234,16 +234,26 @@ TileGeo geo_of(int q, int storage, int nx, int ny, int nz)
 
 }  // namespace
 
-int64_t compact_tile_columns(int q, int storage, int nx, int ny, int nz)
+CompactTiles compact_tiles(int q, int storage, int variant)
 {
-    const TileGeo g = geo_of(q, storage, nx, ny, nz);
+    const int nr = tau1_rowpair_shapes(storage);
+    CompactTiles t;
+    t.shape = variant % nr;
+    t.zchunk = variant < nr ? 24 : 32;
+    t.h = tau1_rowpair_tile_height(q, storage, t.shape);
+    return t;
+}
+
+int64_t compact_tile_columns(const CompactTiles& t, int nx, int ny, int nz)
+{
+    const TileGeo g = geo_of(t, nx, ny, nz);
     if (g.h <= 0) return 0;
     return (int64_t)g.ntiles * ((nz + g.chunk - 1) / g.chunk);
 }
 
-int64_t compact_tile_nodes(int q, int storage, int nx, int ny, int nz, int b)
+int64_t compact_tile_nodes(const CompactTiles& t, int nx, int ny, int nz, int b)
 {
-    const TileGeo g = geo_of(q, storage, nx, ny, nz);
+    const TileGeo g = geo_of(t, nx, ny, nz);
     const int tile = b % g.ntiles;
     const int z0 = (b / g.ntiles) * g.chunk;
     const int x0 = (tile % g.ntx) * 32, y0 = (tile / g.ntx) * g.h;
@@ -253,21 +263,21 @@ int64_t compact_tile_nodes(int q, int storage, int nx, int ny, int nz, int b)
     return w * hh * d;
 }
 
-cudaError_t launch_compact_count(int q, int storage, int nx, int ny, int nz, const uint8_t* flags, int* counts,
+cudaError_t launch_compact_count(const CompactTiles& t, int nx, int ny, int nz, const uint8_t* flags, int* counts,
                                  cudaStream_t s)
 {
-    const TileGeo g = geo_of(q, storage, nx, ny, nz);
-    const int64_t nb = compact_tile_columns(q, storage, nx, ny, nz);
+    const TileGeo g = geo_of(t, nx, ny, nz);
+    const int64_t nb = compact_tile_columns(t, nx, ny, nz);
     if (nb <= 0 || nb > 0x7fffffffLL) return cudaErrorInvalidValue;
     tile_count_kernel<<<(unsigned)nb, CT, 0, s>>>(g, flags, counts);
     return cudaGetLastError();
 }
 
-cudaError_t launch_compact_nodes(int q, int storage, int nx, int ny, int nz, const uint8_t* flags, const int* tiles,
+cudaError_t launch_compact_nodes(const CompactTiles& t, int nx, int ny, int nz, const uint8_t* flags, const int* tiles,
                                  const int* offsets, int ntiles, int* nodes, cudaStream_t s)
 {
     if (ntiles == 0) return cudaSuccess;
-    const TileGeo g = geo_of(q, storage, nx, ny, nz);
+    const TileGeo g = geo_of(t, nx, ny, nz);
     tile_nodes_kernel<<<(unsigned)ntiles, CT, 0, s>>>(g, flags, tiles, offsets, nodes);
     return cudaGetLastError();
 }

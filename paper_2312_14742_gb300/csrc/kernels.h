@@ -27,21 +27,25 @@ int tau1_rowpair_shapes(int storage);
 bool tau1_rowpair_ok(int q, int storage, int shape, const StepArgs& a);
 cudaError_t launch_tau1_rowpair(int q, int storage, int shape, int zchunk, const StepArgs& a, cudaStream_t s);
 // Tile height (2W) of a row-pair shape (0 if none), and the row-pair kernel of
-// shape 0 over a list of tile columns (indices b of the grid order: tile
+// a shape over a list of tile columns (indices b of the grid order: tile
 // b % ntiles, z chunk b / ntiles, ntiles = (nx / 32) (ny / tile height)).
 int tau1_rowpair_tile_height(int q, int storage, int shape);
-cudaError_t launch_tau1_rowpair_list(int q, int storage, int zchunk, const StepArgs& a, const int* list, int count,
-                                     cudaStream_t s);
-// Compact porous layout (compact.cu): tile columns of 32 x H x COMPACT_ZCHUNK
-// nodes (H the row-pair tile height of shape 0), numbered like the row-pair
-// grid; fluid counts per tile column, and the fluid nodes of listed tile
-// columns in row order at the given offsets.
-constexpr int COMPACT_ZCHUNK = 24;
-int64_t compact_tile_columns(int q, int storage, int nx, int ny, int nz);
-int64_t compact_tile_nodes(int q, int storage, int nx, int ny, int nz, int b);
-cudaError_t launch_compact_count(int q, int storage, int nx, int ny, int nz, const uint8_t* flags, int* counts,
+cudaError_t launch_tau1_rowpair_list(int q, int storage, int shape, int zchunk, const StepArgs& a, const int* list,
+                                     int count, cudaStream_t s);
+// Compact porous layout (compact.cu): tile columns of 32 x h x zchunk nodes,
+// the unit of the row-pair variant (shape, zchunk) (variant v of
+// [0, 2 tau1_rowpair_shapes): shape v mod R, zchunk 24 below R, else 32),
+// numbered like that kernel's grid; fluid counts per tile column, and the
+// fluid nodes of listed tile columns in row order at the given offsets.
+struct CompactTiles {
+    int shape, zchunk, h;
+};
+CompactTiles compact_tiles(int q, int storage, int variant);
+int64_t compact_tile_columns(const CompactTiles& t, int nx, int ny, int nz);
+int64_t compact_tile_nodes(const CompactTiles& t, int nx, int ny, int nz, int b);
+cudaError_t launch_compact_count(const CompactTiles& t, int nx, int ny, int nz, const uint8_t* flags, int* counts,
                                  cudaStream_t s);
-cudaError_t launch_compact_nodes(int q, int storage, int nx, int ny, int nz, const uint8_t* flags, const int* tiles,
+cudaError_t launch_compact_nodes(const CompactTiles& t, int nx, int ny, int nz, const uint8_t* flags, const int* tiles,
                                  const int* offsets, int ntiles, int* nodes, cudaStream_t s);
 // Tau1 step of the listed box nodes (fluid), one thread per node, the
 // neighbours gathered from the dense records (the dense kernels' values); the

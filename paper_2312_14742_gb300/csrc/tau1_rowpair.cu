@@ -62,16 +62,17 @@ cudaError_t launch_t(const StepArgs& a, int zchunk, cudaStream_t s, const int* l
 }
 
 template <int Q, int ST>
-cudaError_t launch_s(int shape, int zchunk, const StepArgs& a, cudaStream_t s)
+cudaError_t launch_s(int shape, int zchunk, const StepArgs& a, cudaStream_t s, const int* list = nullptr,
+                     int count = 0)
 {
     if constexpr (ST == ST_F64) {
-        return launch_t<Q, ST, 0>(a, zchunk, s);
+        return shape == 0 ? launch_t<Q, ST, 0>(a, zchunk, s, list, count) : cudaErrorInvalidValue;
     } else {
         switch (shape) {
-        case 0: return launch_t<Q, ST, 0>(a, zchunk, s);
-        case 1: return launch_t<Q, ST, 1>(a, zchunk, s);
-        case 2: return launch_t<Q, ST, 2>(a, zchunk, s);
-        case 3: return launch_t<Q, ST, 3>(a, zchunk, s);
+        case 0: return launch_t<Q, ST, 0>(a, zchunk, s, list, count);
+        case 1: return launch_t<Q, ST, 1>(a, zchunk, s, list, count);
+        case 2: return launch_t<Q, ST, 2>(a, zchunk, s, list, count);
+        case 3: return launch_t<Q, ST, 3>(a, zchunk, s, list, count);
         default: return cudaErrorInvalidValue;
         }
     }
@@ -105,18 +106,19 @@ bool tau1_rowpair_ok(int q, int storage, int shape, const StepArgs& a)
 
 int tau1_rowpair_tile_height(int q, int storage, int shape) { return 2 * shape_w(q, storage, shape); }
 
-cudaError_t launch_tau1_rowpair_list(int q, int storage, int zchunk, const StepArgs& a, const int* list, int count,
-                                     cudaStream_t s)
+cudaError_t launch_tau1_rowpair_list(int q, int storage, int shape, int zchunk, const StepArgs& a, const int* list,
+                                     int count, cudaStream_t s)
 {
+    if (!list) return cudaErrorInvalidValue;
     switch (q * 10 + storage) {
-    case 190 + ST_F64: return launch_t<19, ST_F64, 0>(a, zchunk, s, list, count);
-    case 190 + ST_F32: return launch_t<19, ST_F32, 0>(a, zchunk, s, list, count);
-    case 190 + ST_F16S: return launch_t<19, ST_F16S, 0>(a, zchunk, s, list, count);
-    case 190 + ST_BF16S: return launch_t<19, ST_BF16S, 0>(a, zchunk, s, list, count);
-    case 270 + ST_F64: return launch_t<27, ST_F64, 0>(a, zchunk, s, list, count);
-    case 270 + ST_F32: return launch_t<27, ST_F32, 0>(a, zchunk, s, list, count);
-    case 270 + ST_F16S: return launch_t<27, ST_F16S, 0>(a, zchunk, s, list, count);
-    case 270 + ST_BF16S: return launch_t<27, ST_BF16S, 0>(a, zchunk, s, list, count);
+    case 190 + ST_F64: return launch_s<19, ST_F64>(shape, zchunk, a, s, list, count);
+    case 190 + ST_F32: return launch_s<19, ST_F32>(shape, zchunk, a, s, list, count);
+    case 190 + ST_F16S: return launch_s<19, ST_F16S>(shape, zchunk, a, s, list, count);
+    case 190 + ST_BF16S: return launch_s<19, ST_BF16S>(shape, zchunk, a, s, list, count);
+    case 270 + ST_F64: return launch_s<27, ST_F64>(shape, zchunk, a, s, list, count);
+    case 270 + ST_F32: return launch_s<27, ST_F32>(shape, zchunk, a, s, list, count);
+    case 270 + ST_F16S: return launch_s<27, ST_F16S>(shape, zchunk, a, s, list, count);
+    case 270 + ST_BF16S: return launch_s<27, ST_BF16S>(shape, zchunk, a, s, list, count);
     default: return cudaErrorInvalidValue;
     }
 }

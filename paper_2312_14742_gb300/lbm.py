@@ -53,7 +53,8 @@ class lbm_tau1_stats(ctypes.Structure):
 
 
 class lbm_tau1_compact_info(ctypes.Structure):
-    _fields_ = [("threshold", ctypes.c_double), ("tile", ctypes.c_int32 * 3), ("tiled_ok", ctypes.c_int32),
+    _fields_ = [("threshold", ctypes.c_double), ("variant", ctypes.c_int32), ("tile", ctypes.c_int32 * 3),
+                ("tiled_ok", ctypes.c_int32),
                 ("columns", ctypes.c_int64), ("empty_columns", ctypes.c_int64), ("full_columns", ctypes.c_int64),
                 ("tiled_columns", ctypes.c_int64),
                 ("listed_columns", ctypes.c_int64), ("tiled_nodes", ctypes.c_int64), ("tiled_fluid", ctypes.c_int64),

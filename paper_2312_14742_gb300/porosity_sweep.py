@@ -12,9 +12,9 @@ for the sparse layout (the neighbour indices).
 
 The compact layout (dense records, work split by tile column: no fluid ->
 skipped, fluid fraction >= f* -> tiled kernel, else a 4-byte node list) is
-timed at the threshold its autotune picks, and at f* = 0 (every non-empty
-tile column tiled: the paper's chunk skipping, Section 3.2) and f* = 1.01
-(every fluid node through the list). Its algorithmic bytes are the dense
+timed at the tile variant and threshold its autotune picks, and with that
+variant at f* = 0 (every non-empty tile column tiled: the paper's chunk
+skipping, Section 3.2) and f* = 1.01 (every fluid node through the list). Its algorithmic bytes are the dense
 layout's 32 B per fluid node, plus 1 B per node of the tiled columns and 4 B
 per listed node.
 
@@ -84,9 +84,12 @@ def sweep(size: int, radius: float, phis, steps: int, warmup: int, q: int = 19, 
                "n_fluid": nf, "geometry_s": gen_s}
         runs = (("dense", 0, None), ("sparse", LBM_SPARSE, None), ("compact", LBM_COMPACT, "tune"),
                 ("compact_tiles", LBM_COMPACT, 0.0), ("compact_list", LBM_COMPACT, 1.01))
+        tuned_variant = 0
         for name, layout, thr in runs:
             with Tau1(q, dims, storage=storage, g=(g, 0, 0), layout=layout, stream=stream) as t:
                 if isinstance(thr, float):
+                    # the fixed-threshold runs take the tile variant the tuned run chose
+                    t.set_variant(tuned_variant)
                     t.set_compact_threshold(thr)
                 t.set_geometry(solid)
                 if layout == 0 or thr == "tune":
@@ -95,6 +98,8 @@ def sweep(size: int, radius: float, phis, steps: int, warmup: int, q: int = 19, 
                 dt = measure(t, k, warmup if thr in (None, "tune") else warmup // 8, stream)
                 st = t.reduce(allow_diverged=True)
                 ci = t.compact_info() if layout == LBM_COMPACT else None
+                if thr == "tune":
+                    tuned_variant = ci["variant"]
             if layout == 0:
                 algo = 8 * s * nf + n
             elif layout == LBM_SPARSE:

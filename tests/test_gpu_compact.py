@@ -88,6 +88,38 @@ def test_compact_bitwise_equals_dense_every_threshold(q, storage):
     assert seen == {(True, False), (True, True), (False, True)}
 
 
+@pytest.mark.parametrize("storage", ("f32", "f64", "bf16s"))
+def test_compact_every_variant_bitwise_equals_dense(storage):
+    """Every row-pair variant (tile shape, 24- or 32-plane chunks) as the
+    compact layout's tile column; a shape whose tile height does not divide
+    ny = 48 sends every column to the node list."""
+    solid = mixed_medium(64, 48, 70, 7150)
+    st = lbm_inputs.random_fields(solid.shape, 7151, 2e-3, 3e-3, solid)
+    g = (1e-5, -2e-6, 3e-6)
+    ref, _, _ = run(19, solid, (1, 1, 1), g, storage, 20, st)
+    nz, ny, nx = solid.shape
+    nf = int(np.count_nonzero(solid == 0))
+    nv = 2 if storage == "f64" else 8
+    for v in range(nv):
+        # a fresh handle per variant: the 16-bit stochastic rounding draws on the step count
+        with Tau1(19, (nx, ny, nz), storage=storage, g=g, layout=LBM_COMPACT) as t:
+            assert t.variant_count == nv
+            t.set_variant(v)
+            t.set_geometry(solid)
+            t.set_fields(*st)
+            t.step(20)
+            got = t.get_fields()
+            info = t.compact_info()
+            # switching the variant with a geometry set rebuilds the lists; the state is kept
+            t.set_variant((v + 1) % nv)
+            assert t.compact_info()["variant"] == (v + 1) % nv
+            assert_same(t.get_fields(), got, (storage, v, "kept"))
+            assert_same(got, ref, (storage, v))
+            assert info["variant"] == v and info["tile"][2] == (24 if v < nv // 2 else 32)
+            assert info["tiled_fluid"] + info["listed_nodes"] == nf
+            assert info["tiled_ok"] == (1 if 48 % info["tile"][1] == 0 else 0)
+
+
 @pytest.mark.parametrize("storage", ("f32", "f64"))
 @pytest.mark.parametrize("dims,per,phi", [((45, 19, 21), (1, 0, 1), 0.5), ((64, 12, 9), (0, 1, 0), 0.7),
                                           ((32, 16, 1), (1, 1, 1), 0.6)])
