@@ -44,6 +44,8 @@ def parse():
     p.add_argument("--q", type=int, default=19)
     p.add_argument("--storage", default="f32")
     p.add_argument("--kernel", default="auto")
+    p.add_argument("--variant", type=int, default=-1,
+                   help="tile variant of the step kernel (profiling a fixed kernel); -1: autotune")
     p.add_argument("--size", type=int, default=256)
     p.add_argument("--porosity", type=float, default=0.9)
     p.add_argument("--radius", type=float, default=8.0)
@@ -278,7 +280,11 @@ def run_ours(args):
              kernel=args.kernel, stream=stream)
     t.set_geometry(solid)
     t.step(min(args.warmup, 50))
-    variant, tuned_ms = t.autotune(20)
+    if args.variant >= 0:
+        t.set_variant(args.variant)
+        variant, tuned_ms = args.variant, None
+    else:
+        variant, tuned_ms = t.autotune(20)
     t.step(args.warmup)
     barrier()
 
