@@ -17,9 +17,11 @@
 // The step kernel updates the face nodes like any other (the faces of a
 // non-periodic axis are walls to it); this kernel runs after it on the same
 // stream, reads the same pre state, and overwrites the face nodes of the post
-// state. One thread per face node. The face arithmetic is FP64 for every
-// storage format: u is the difference of two sums of about rho_b - 1 each,
-// and the faces are a small share of the nodes.
+// state. One thread per face node; a block first evaluates the moments of
+// every source node of its 32 x 8 patch of the face once, into shared memory.
+// The face arithmetic is FP64 for every storage format: u is the difference
+// of two sums of about rho_b - 1 each, and the faces are a small share of the
+// nodes.
 #include "kernels.h"
 #include "static_for.cuh"
 #include "tau1_node.cuh"
@@ -28,69 +30,117 @@ namespace lbm {
 
 namespace {
 
+// Face tile of one block: FU x FV face nodes along the in-face axes, with a
+// one-node ring, in the face plane (j = 0) and the plane inside it (j = 1):
+// the sources of every known population.
+constexpr int FU = 32, FV = 8, SU = FU + 2, SV = FV + 2;
+
+struct FaceMoments {
+    double A[2][SV][SU], Px[2][SV][SU], Py[2][SV][SU], Pz[2][SV][SU], H[2][SV][SU];
+    unsigned char wall[2][SV][SU];  // outside a non-periodic face, or solid
+};
+
+// Box coordinates (x, y, z) of the node at coordinate ca along the face axis
+// and (cu, cv) along the in-face axes (the other two, in x, y, z order).
+__device__ __forceinline__ uint32_t face_node(const StepArgs& a, int axis, int ca, int cu, int cv)
+{
+    const int x = axis == 0 ? ca : cu;
+    const int y = axis == 0 ? cu : (axis == 1 ? ca : cv);
+    const int z = axis == 2 ? ca : cv;
+    return (uint32_t)x + (uint32_t)a.nx * ((uint32_t)y + (uint32_t)a.ny * (uint32_t)z);
+}
+
+// c (-1 <= c <= n) into [0, n) on a periodic axis; false if c lies outside a
+// non-periodic one
+__device__ __forceinline__ bool wrap_axis(int& c, int n, bool per)
+{
+    if (c >= 0 && c < n) return true;
+    if (!per) return false;
+    c = c < 0 ? c + n : c - n;
+    return true;
+}
+
 template <int Q, int ST>
-__global__ void __launch_bounds__(256) zou_he_kernel(StepArgs a, int axis, double rho_lo, double rho_hi)
+__global__ void __launch_bounds__(FU * FV) zou_he_kernel(StepArgs a, int axis, double rho_lo, double rho_hi, int tiles_u,
+                                                          int tiles_v)
 {
     using S = Storage<ST>;
     using C = typename S::ctype;  // stored values
     using T = double;             // face arithmetic
     using LT = Lat<Q>;
-    const int n[3] = {a.nx, a.ny, a.nz};
-    const int ua = axis == 0 ? 1 : 0, va = axis == 2 ? 1 : 2;  // in-face axes
-    const int64_t face = (int64_t)n[ua] * n[va];
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= 2 * face) return;
-    const int side = t >= face ? 1 : 0;
-    if (side && n[axis] == 1) return;  // one plane: the low face only
-    t -= side * face;
-    int pos[3];
-    pos[axis] = side ? n[axis] - 1 : 0;
-    pos[ua] = (int)(t % n[ua]);
-    pos[va] = (int)(t / n[ua]);
-    const uint32_t i = (uint32_t)pos[0] + (uint32_t)a.nx * ((uint32_t)pos[1] + (uint32_t)a.ny * (uint32_t)pos[2]);
+    __shared__ FaceMoments fm;
+    // sizes and periodicity along the face axis and the in-face axes u, v
+    const int na = axis == 0 ? a.nx : (axis == 1 ? a.ny : a.nz);
+    const int nu = axis == 0 ? a.ny : a.nx;
+    const int nv = axis == 2 ? a.ny : a.nz;
+    const bool per_u = (axis == 0 ? a.periodic[1] : a.periodic[0]) != 0;
+    const bool per_v = (axis == 2 ? a.periodic[1] : a.periodic[2]) != 0;
+    int b = blockIdx.x;
+    const int side = b / (tiles_u * tiles_v);
+    b -= side * tiles_u * tiles_v;
+    if (side && na == 1) return;  // one plane: the low face only (the whole block leaves)
+    const int u0 = (b % tiles_u) * FU, v0 = (b / tiles_u) * FV;
+    const int sgn = side ? -1 : 1;
+    const int pa = side ? na - 1 : 0;
     const Scales sc(a.dscale);
-    C c0, c1, c2v, c3;
-    S::load(a.pre, i, sc.inv, c0, c1, c2v, c3);
-    if (isnan(c0)) return;  // solid face node
-    const T d0 = c0, ux0 = c1, uy0 = c2v, uz0 = c3;
     // the step kernels evaluate g in the compute precision of the format
     const T gx = (T)gcomp<C>(a, 0), gy = (T)gcomp<C>(a, 1), gz = (T)gcomp<C>(a, 2);
-    const NodeMoments<T> own = node_moments<T>(d0, ux0, uy0, uz0, gx, gy, gz);
-    const int sgn = side ? -1 : 1;
+
+    // every source node's moments, once per block (the face axis is not
+    // periodic: the inner plane lies outside only when the box is one plane)
+    for (int c = threadIdx.x; c < 2 * SV * SU; c += FU * FV) {
+        const int j = c / (SV * SU), r = c - j * (SV * SU), sv = r / SU, su = r - sv * SU;
+        const int ca = pa + (j ? sgn : 0);
+        int cu = u0 + su - 1, cv = v0 + sv - 1;
+        // cells beyond the ring of the face (a patch wider than the face) are
+        // the source of no face node: left as walls, never loaded
+        const bool near = cu <= nu && cv <= nv;
+        const bool inside = near && ca >= 0 && ca < na && wrap_axis(cu, nu, per_u) && wrap_axis(cv, nv, per_v);
+        bool wall = !inside;
+        NodeMoments<T> m{T(0), T(0), T(0), T(0), T(0)};
+        if (inside) {
+            C e0, e1, e2, e3;
+            S::load(a.pre, face_node(a, axis, ca, cu, cv), sc.inv, e0, e1, e2, e3);
+            wall = isnan(e0);
+            if (!wall) m = node_moments<T>((T)e0, (T)e1, (T)e2, (T)e3, gx, gy, gz);
+        }
+        fm.A[j][sv][su] = m.A;
+        fm.Px[j][sv][su] = m.Px;
+        fm.Py[j][sv][su] = m.Py;
+        fm.Pz[j][sv][su] = m.Pz;
+        fm.H[j][sv][su] = m.H;
+        fm.wall[j][sv][su] = wall ? 1 : 0;
+    }
+    __syncthreads();
+
+    const int tu = threadIdx.x % FU, tv = threadIdx.x / FU;
+    if (u0 + tu >= nu || v0 + tv >= nv) return;
+    if (fm.wall[0][tv + 1][tu + 1]) return;  // solid face node
+    const uint32_t i = face_node(a, axis, pa, u0 + tu, v0 + tv);
+    NodeMoments<T> own;
+    own.A = fm.A[0][tv + 1][tu + 1];
+    own.Px = fm.Px[0][tv + 1][tu + 1];
+    own.Py = fm.Py[0][tv + 1][tu + 1];
+    own.Pz = fm.Pz[0][tv + 1][tu + 1];
+    own.H = fm.H[0][tv + 1][tu + 1];
     T h0 = T(LT::w(0)) * own.A, hout = T(0);  // rest: the node's own equilibrium
     static_for<1, Q>([&](auto kc) {
         constexpr int K = decltype(kc)::value;
-        const int ck = LT::c(K, axis);
+        constexpr int cx = LT::c(K, 0), cy = LT::c(K, 1), cz = LT::c(K, 2);
+        const int ck = axis == 0 ? cx : (axis == 1 ? cy : cz);
         if (ck == sgn) return;  // unknown: enters from outside
-        int sp[3] = {pos[0] - LT::c(K, 0), pos[1] - LT::c(K, 1), pos[2] - LT::c(K, 2)};
-        bool inside = true;
-#pragma unroll
-        for (int d = 0; d < 3; ++d)
-            if (sp[d] < 0 || sp[d] >= n[d]) {
-                if (a.periodic[d]) sp[d] = sp[d] < 0 ? sp[d] + n[d] : sp[d] - n[d];
-                else inside = false;
-            }
+        // source x - c_K: the face plane (c_K along the axis 0) or the inner plane
+        const int j = ck == 0 ? 0 : 1;
+        const int su = tu + 1 - (axis == 0 ? cy : cx), sv = tv + 1 - (axis == 2 ? cy : cz);
         T v;
-        bool wall = !inside;
-        T ds = T(0), uxs = T(0), uys = T(0), uzs = T(0);
-        if (inside) {
-            C e0, e1, e2, e3;
-            S::load(a.pre, (uint32_t)sp[0] + (uint32_t)a.nx * ((uint32_t)sp[1] + (uint32_t)a.ny * (uint32_t)sp[2]),
-                    sc.inv, e0, e1, e2, e3);
-            ds = e0;
-            uxs = e1;
-            uys = e2;
-            uzs = e3;
-            wall = isnan(ds);
-        }
-        if (wall) {
+        if (fm.wall[j][sv][su]) {
             // halfway bounce-back: own previous state in direction inv(K), p(inv K) = -p(K)
-            const T p = T(LT::c(K, 0)) * own.Px + T(LT::c(K, 1)) * own.Py + T(LT::c(K, 2)) * own.Pz;
+            const T p = T(cx) * own.Px + T(cy) * own.Py + T(cz) * own.Pz;
             v = feq_scaled(own.A, own.H, -p);
         } else {
-            const NodeMoments<T> m = node_moments<T>(ds, uxs, uys, uzs, gx, gy, gz);
-            const T p = T(LT::c(K, 0)) * m.Px + T(LT::c(K, 1)) * m.Py + T(LT::c(K, 2)) * m.Pz;
-            v = feq_scaled(m.A, m.H, p);
+            const T Px = fm.Px[j][sv][su], Py = fm.Py[j][sv][su], Pz = fm.Pz[j][sv][su];
+            const T p = T(cx) * Px + T(cy) * Py + T(cz) * Pz;
+            v = feq_scaled(fm.A[j][sv][su], fm.H[j][sv][su], p);
         }
         v = T(LT::w(K)) * v;
         if (ck == 0) h0 += v;
@@ -99,23 +149,23 @@ __global__ void __launch_bounds__(256) zou_he_kernel(StepArgs a, int axis, doubl
     const T rho_b = T(side ? rho_hi : rho_lo);
     const T drho_b = T((side ? rho_hi : rho_lo) - 1.0);
     const T u = T(sgn) * (drho_b - h0 - T(2) * hout) / rho_b;
-    C out[3] = {C(0), C(0), C(0)};
-    out[axis] = (C)u;
-    step_store<ST>(a.post, i, (C)drho_b, out[0], out[1], out[2], sc.s, a.seed);
+    const C cu = (C)u;
+    step_store<ST>(a.post, i, (C)drho_b, axis == 0 ? cu : C(0), axis == 1 ? cu : C(0), axis == 2 ? cu : C(0), sc.s,
+                   a.seed);
 }
 
 template <int Q>
 cudaError_t launch_q(int storage, const StepArgs& a, int axis, double lo, double hi, cudaStream_t s)
 {
-    const int n[3] = {a.nx, a.ny, a.nz};
-    const int ua = axis == 0 ? 1 : 0, va = axis == 2 ? 1 : 2;
-    const int64_t threads = 2 * (int64_t)n[ua] * n[va];
-    const unsigned blocks = (unsigned)((threads + 255) / 256);
+    const int nu = axis == 0 ? a.ny : a.nx, nv = axis == 2 ? a.ny : a.nz;  // in-face axes
+    const int tu = (nu + FU - 1) / FU, tv = (nv + FV - 1) / FV;
+    const int64_t blocks = 2 * (int64_t)tu * tv;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     switch (storage) {
-    case ST_F64: zou_he_kernel<Q, ST_F64><<<blocks, 256, 0, s>>>(a, axis, lo, hi); break;
-    case ST_F32: zou_he_kernel<Q, ST_F32><<<blocks, 256, 0, s>>>(a, axis, lo, hi); break;
-    case ST_F16S: zou_he_kernel<Q, ST_F16S><<<blocks, 256, 0, s>>>(a, axis, lo, hi); break;
-    case ST_BF16S: zou_he_kernel<Q, ST_BF16S><<<blocks, 256, 0, s>>>(a, axis, lo, hi); break;
+    case ST_F64: zou_he_kernel<Q, ST_F64><<<(unsigned)blocks, FU * FV, 0, s>>>(a, axis, lo, hi, tu, tv); break;
+    case ST_F32: zou_he_kernel<Q, ST_F32><<<(unsigned)blocks, FU * FV, 0, s>>>(a, axis, lo, hi, tu, tv); break;
+    case ST_F16S: zou_he_kernel<Q, ST_F16S><<<(unsigned)blocks, FU * FV, 0, s>>>(a, axis, lo, hi, tu, tv); break;
+    case ST_BF16S: zou_he_kernel<Q, ST_BF16S><<<(unsigned)blocks, FU * FV, 0, s>>>(a, axis, lo, hi, tu, tv); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
