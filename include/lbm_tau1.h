@@ -340,6 +340,25 @@ lbm_status lbm_tau1_batch_step(lbm_tau1_batch* b, int64_t nsteps);
  * LBM_EDIVERGED, with every out[] filled, if any of them diverged. */
 lbm_status lbm_tau1_batch_stats(lbm_tau1_batch* b, int32_t n, const int32_t* slots, lbm_tau1_stats* out);
 
+/* The same statistics without waiting: queues the reductions of the n live
+ * boxes slots[0..n-1] on the batch's stream, with their copy into page-locked
+ * memory of the batch and an event after it, and returns. Steps queued after
+ * this call do not change the result: each box is reduced as it stands when
+ * its reduction runs, which is after the steps queued before this call. The
+ * host can queue the next steps, release and admit boxes, and then take the
+ * result with lbm_tau1_batch_stats_wait, which waits for the event only and
+ * fills out[0..n-1] in the order of slots (a released box is reduced before
+ * its memory is freed: both are ordered on the stream). One queued request at
+ * a time: LBM_ESTATE if one is already waiting. Errors: LBM_EINVAL (bad
+ * arguments, slot not live), LBM_ECUDA. */
+lbm_status lbm_tau1_batch_stats_queue(lbm_tau1_batch* b, int32_t n, const int32_t* slots);
+
+/* Waits for the statistics queued by lbm_tau1_batch_stats_queue and fills
+ * out[0..n-1] (n as queued). Returns LBM_EDIVERGED, with every out[] filled,
+ * if any box diverged; LBM_ETIMEOUT if a staged-copy wait ran out in the
+ * steps before the reductions; LBM_ESTATE if nothing was queued. */
+lbm_status lbm_tau1_batch_stats_wait(lbm_tau1_batch* b, lbm_tau1_stats* out);
+
 /* State of a live box as doubles, as lbm_tau1_get_fields. */
 lbm_status lbm_tau1_batch_get_fields(lbm_tau1_batch* b, int32_t slot, double* drho, double* ux, double* uy,
                                      double* uz, int on_device);

@@ -72,6 +72,15 @@ struct lbm_tau1_batch {
     double* red_out = nullptr;   // device [capacity][RED_FIELDS]
     double* red_host = nullptr;  // pinned copy
     unsigned int* dtimeouts = nullptr;  // device counter of staged-copy waits that ran out
+    // queued statistics (stats_queue / stats_wait): their own device and
+    // pinned buffers ([capacity][RED_FIELDS], then the timeout count), the
+    // event after the copy, and what the host needs to finish them
+    double* qred_out = nullptr;
+    double* qred_host = nullptr;
+    cudaEvent_t qev = nullptr;
+    bool qpending = false;
+    std::vector<int64_t> qn, qsteps;
+    std::vector<lbm_tau1_config> qcfg;
     int nlive = 0;
     int64_t launches = 0;
     std::string err;
@@ -285,6 +294,9 @@ void free_batch(lbm_tau1_batch* b)
     if (b->red_partials) cudaFree(b->red_partials);
     if (b->red_out) cudaFree(b->red_out);
     if (b->red_host) cudaFreeHost(b->red_host);
+    if (b->qred_out) cudaFree(b->qred_out);
+    if (b->qred_host) cudaFreeHost(b->qred_host);
+    if (b->qev) cudaEventDestroy(b->qev);
     if (b->dtimeouts) cudaFree(b->dtimeouts);
     if (b->side_done) cudaEventDestroy(b->side_done);
     if (b->side) cudaStreamDestroy(b->side);
@@ -361,6 +373,9 @@ lbm_status lbm_tau1_batch_create(const lbm_tau1_batch_config* cfg, lbm_tau1_batc
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->dtimeouts, sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMemsetAsync(b->dtimeouts, 0, sizeof(unsigned int), b->stream);
     if (e == cudaSuccess) e = cudaMallocHost(&b->red_host, (size_t)cap * RED_FIELDS * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&b->qred_out, ((size_t)cap * RED_FIELDS + 1) * sizeof(double));
+    if (e == cudaSuccess) e = cudaMallocHost(&b->qred_host, ((size_t)cap * RED_FIELDS + 1) * sizeof(double));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->qev, cudaEventDisableTiming);
     if (e == cudaSuccess && cfg->hbm_budget == 0) {
         size_t fr = 0, tot = 0;
         e = cudaMemGetInfo(&fr, &tot);
@@ -569,6 +584,59 @@ lbm_status lbm_tau1_batch_stats(lbm_tau1_batch* b, int32_t n, const int32_t* slo
             worst = LBM_EDIVERGED;
     }
     if (worst != LBM_OK) return bfail(b, worst, "batch_stats: a box diverged (non-finite value or |u| > 0.3)");
+    return LBM_OK;
+}
+
+lbm_status lbm_tau1_batch_stats_queue(lbm_tau1_batch* b, int32_t n, const int32_t* slots)
+{
+    if (!b) return bfail(nullptr, LBM_EINVAL, "batch_stats_queue: NULL batch");
+    if (b->qpending) return bfail(b, LBM_ESTATE, "batch_stats_queue: the previous queued statistics were not taken");
+    if (n < 0 || n > b->cfg.capacity || (n > 0 && !slots)) return bfail(b, LBM_EINVAL, "batch_stats_queue: bad arguments");
+    for (int i = 0; i < n; ++i)
+        if (lbm_status st = live_slot(b, slots[i], "batch_stats_queue")) return st;
+    b->qn.assign((size_t)n, 0);
+    b->qsteps.assign((size_t)n, 0);
+    b->qcfg.assign((size_t)n, lbm_tau1_config{});
+    for (int i = 0; i < n; ++i) {
+        const Slot& s = b->slots[slots[i]];
+        const void* f[4] = {s.buf[s.steps & 1], nullptr, nullptr, nullptr};
+        cudaError_t e = launch_reduce(b->cfg.storage, true, s.n, f, nullptr, s.flags, s.cfg.g, b->red_partials,
+                                      b->qred_out + (size_t)i * RED_FIELDS, b->stream, dinv_of(b, slots[i]));
+        b->launches += 2;
+        if (e != cudaSuccess) return bcuda(b, e, "batch_stats_queue: kernel");
+        b->qn[(size_t)i] = s.n;
+        b->qsteps[(size_t)i] = s.steps;
+        b->qcfg[(size_t)i] = s.cfg;
+    }
+    // the statistics and the timeout count (as a double after them), then the count cleared
+    const size_t tail = (size_t)n * RED_FIELDS;
+    BCUDA(b, cudaMemcpyAsync(b->qred_host, b->qred_out, tail * sizeof(double), cudaMemcpyDefault, b->stream),
+          "batch_stats_queue: copy");
+    unsigned int* tcount = reinterpret_cast<unsigned int*>(b->qred_host + tail);
+    BCUDA(b, cudaMemcpyAsync(tcount, b->dtimeouts, sizeof(unsigned int), cudaMemcpyDefault, b->stream),
+          "batch_stats_queue: copy");
+    BCUDA(b, cudaMemsetAsync(b->dtimeouts, 0, sizeof(unsigned int), b->stream), "batch_stats_queue: clear");
+    BCUDA(b, cudaEventRecord(b->qev, b->stream), "batch_stats_queue: event");
+    b->qpending = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_tau1_batch_stats_wait(lbm_tau1_batch* b, lbm_tau1_stats* out)
+{
+    if (!b) return bfail(nullptr, LBM_EINVAL, "batch_stats_wait: NULL batch");
+    if (!b->qpending) return bfail(b, LBM_ESTATE, "batch_stats_wait: no statistics queued");
+    const int n = (int)b->qn.size();
+    if (n > 0 && !out) return bfail(b, LBM_EINVAL, "batch_stats_wait: NULL output");
+    b->qpending = false;
+    BCUDA(b, cudaEventSynchronize(b->qev), "batch_stats_wait: sync");
+    const unsigned int t = *reinterpret_cast<const unsigned int*>(b->qred_host + (size_t)n * RED_FIELDS);
+    if (t) return bfail(b, LBM_ETIMEOUT, "batch_stats_wait: " + std::to_string(t) + " staged-copy waits ran out");
+    lbm_status worst = LBM_OK;
+    for (int i = 0; i < n; ++i)
+        if (fill_stats(b->qred_host + (size_t)i * RED_FIELDS, b->qn[(size_t)i], b->qcfg[(size_t)i].g,
+                       b->qsteps[(size_t)i], &out[i]) != LBM_OK)
+            worst = LBM_EDIVERGED;
+    if (worst != LBM_OK) return bfail(b, worst, "batch_stats_wait: a box diverged (non-finite value or |u| > 0.3)");
     return LBM_OK;
 }
 

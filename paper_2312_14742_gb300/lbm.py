@@ -103,6 +103,8 @@ SIGNATURES = {
     "lbm_tau1_batch_admit": (_I, [_H, ctypes.POINTER(lbm_tau1_config), _P, _I, ctypes.POINTER(ctypes.c_int32)]),
     "lbm_tau1_batch_step": (_I, [_H, _I64]),
     "lbm_tau1_batch_stats": (_I, [_H, ctypes.c_int32, _P, _P]),
+    "lbm_tau1_batch_stats_queue": (_I, [_H, ctypes.c_int32, _P]),
+    "lbm_tau1_batch_stats_wait": (_I, [_H, _P]),
     "lbm_tau1_batch_get_fields": (_I, [_H, ctypes.c_int32, _P, _P, _P, _P, _I]),
     "lbm_tau1_batch_release": (_I, [_H, ctypes.c_int32]),
     "lbm_tau1_batch_synchronize": (_I, [_H]),
@@ -258,6 +260,14 @@ def lbm_tau1_batch_step(b, nsteps: int) -> int:
 
 def lbm_tau1_batch_stats(b, n: int, slots_ptr, stats_ptr) -> int:
     return _fn("lbm_tau1_batch_stats")(b, n, slots_ptr, stats_ptr)
+
+
+def lbm_tau1_batch_stats_queue(b, n: int, slots_ptr) -> int:
+    return _fn("lbm_tau1_batch_stats_queue")(b, n, slots_ptr)
+
+
+def lbm_tau1_batch_stats_wait(b, stats_ptr) -> int:
+    return _fn("lbm_tau1_batch_stats_wait")(b, stats_ptr)
 
 
 def lbm_tau1_batch_get_fields(b, slot: int, drho, ux, uy, uz, on_device: int) -> int:
@@ -503,6 +513,25 @@ class Batch:
         if not (st == LBM_EDIVERGED and allow_diverged):
             self._check(st)
         return [o.as_dict() for o in out]
+
+    def stats_queue(self, slots) -> None:
+        """Queues the statistics of the given live slots and returns without
+        waiting; stats_wait() takes them (steps, releases and admissions may
+        be queued in between)."""
+        slots = list(slots)
+        arr = (ctypes.c_int32 * max(1, len(slots)))(*slots)
+        self._check(lbm_tau1_batch_stats_queue(self.b, len(slots), ctypes.cast(arr, _P)))
+        self._queued = len(slots)
+
+    def stats_wait(self, allow_diverged: bool = False) -> list[dict]:
+        """The statistics queued by stats_queue, in the order of its slots."""
+        n = getattr(self, "_queued", 0)
+        out = (lbm_tau1_stats * max(1, n))()
+        st = lbm_tau1_batch_stats_wait(self.b, ctypes.cast(out, _P))
+        self._queued = 0
+        if not (st == LBM_EDIVERGED and allow_diverged):
+            self._check(st)
+        return [out[i].as_dict() for i in range(n)]
 
     def get_fields(self, slot: int):
         arrs = [np.empty(self.shapes[slot], dtype=np.float64) for _ in range(4)]

@@ -24,6 +24,14 @@ stored state carries stochastic-rounding noise, so the mean U of N_f fluid
 nodes fluctuates by about 2^-p / sqrt(N_f) relative (p = 11 FP16, 8 BF16);
 the tolerance is raised to 8 times that floor where it exceeds tol.
 
+Host and device overlap (the default): the server queues a chunk and the
+statistics behind it (into page-locked memory, with an event:
+``Batch.stats_queue`` / ``stats_wait``), admits waiting requests while the
+chunk runs (mask upload, allocation and table edit; an admitted box joins
+the next chunk), then waits for the statistics and releases the converged
+boxes before it queues the next chunk, so no box is stepped past its answer.
+``overlap=False`` admits only after each chunk's statistics have come back.
+
 The host logic here only schedules; every step and reduction runs in the
 CUDA library. Geometry is generated ahead of arrival on worker threads (the
 generator runs in C and releases the GIL), so latency measures the server.
@@ -163,7 +171,8 @@ class BatchedServer:
 
     def __init__(self, q: int = 19, storage: str = "f32", capacity: int = 256, chunk: int = 100, tol: float = 1e-6,
                  cap: int = 20000, g: float = 1e-5, hbm_budget: int = 0, variant: int = 0, batch=None,
-                 clock=time.perf_counter, sleep=time.sleep, max_live_nodes: int | None = 2 ** 25):
+                 clock=time.perf_counter, sleep=time.sleep, max_live_nodes: int | None = 2 ** 25,
+                 overlap: bool = True):
         if batch is None:
             from .lbm import Batch
 
@@ -177,9 +186,12 @@ class BatchedServer:
         self.clock = clock
         self.sleep = sleep
         self.max_live_nodes = max_live_nodes
+        self.overlap = overlap
         self.fluid_updates = 0
 
     def run(self, requests: list[Request], geometry_fn=geometry, prefetch: int = 8, workers: int = 4) -> list[Result]:
+        if self.overlap:
+            return self._run_overlapped(requests, geometry_fn, prefetch, workers)
         order = sorted(requests, key=lambda r: (r.arrival, r.id))
         pre = _Prefetch(order, geometry_fn, prefetch, workers)
         t0 = self.clock()
@@ -231,6 +243,76 @@ class BatchedServer:
                     results.append(Result(req.id, req.edge, st["n_fluid"], steps, status, st["permeability"],
                                           st["mean_ux_superficial"], st["max_abs_u"], req.arrival, admitted, now))
                     self.batch.release(slot)
+                    del live[slot]
+        finally:
+            pre.close()
+        return results
+
+
+    def _run_overlapped(self, requests, geometry_fn, prefetch, workers) -> list[Result]:
+        order = sorted(requests, key=lambda r: (r.arrival, r.id))
+        pre = _Prefetch(order, geometry_fn, prefetch, workers)
+        t0 = self.clock()
+        nxt = 0
+        queue: deque = deque()
+        live: dict[int, list] = {}  # slot -> [request, convergence, admitted, steps queued]
+        results: list[Result] = []
+
+        def admit_waiting():
+            nonlocal nxt
+            now = self.clock() - t0
+            while nxt < len(order) and order[nxt].arrival <= now:
+                queue.append((nxt, order[nxt], None))
+                nxt += 1
+            live_nodes = sum(v[0].edge ** 3 for v in live.values())
+            while queue:
+                k, req, mask = queue[0]
+                if live and self.max_live_nodes and live_nodes + req.edge ** 3 > self.max_live_nodes:
+                    break
+                if mask is None:
+                    mask = pre.get(k, req)
+                    queue[0] = (k, req, mask)
+                slot = self.batch.admit(mask, (1, 1, 1), (self.g, 0.0, 0.0))
+                if slot is None:
+                    if not live:
+                        raise RuntimeError(f"request {req.id} (edge {req.edge}) does not fit an empty batch")
+                    break
+                queue.popleft()
+                live[slot] = [req, None, self.clock() - t0, 0]
+                live_nodes += req.edge ** 3
+
+        try:
+            while len(results) < len(order):
+                if not live:
+                    admit_waiting()
+                    if not live:
+                        if nxt < len(order):
+                            self.sleep(max(0.0, order[nxt].arrival - (self.clock() - t0)))
+                        continue
+                # a chunk of every live box, and its statistics behind it
+                self.batch.step(self.chunk)
+                slots = list(live)
+                for sl in slots:
+                    live[sl][3] += self.chunk
+                self.batch.stats_queue(slots)
+                steps_at = [live[sl][3] for sl in slots]
+                # while it runs: admissions (they join the next chunk)
+                admit_waiting()
+                stats = self.batch.stats_wait(allow_diverged=True)
+                now = self.clock() - t0
+                for slot, st, steps in zip(slots, stats, steps_at):
+                    req, conv, admitted, _ = live[slot]
+                    if conv is None:
+                        conv = Convergence(self.tol, self.cap, self.storage, st["n_fluid"])
+                        live[slot][1] = conv
+                    finite = st["nonfinite"] == 0 and st["max_abs_u"] <= 0.3
+                    status = conv.update(st["mean_ux_superficial"], steps, finite)
+                    self.fluid_updates += st["n_fluid"] * self.chunk
+                    if status is None:
+                        continue
+                    results.append(Result(req.id, req.edge, st["n_fluid"], steps, status, st["permeability"],
+                                          st["mean_ux_superficial"], st["max_abs_u"], req.arrival, admitted, now))
+                    self.batch.release(slot)  # before the next chunk is queued
                     del live[slot]
         finally:
             pre.close()
@@ -317,11 +399,13 @@ def calibrate(requests: list[Request], **server_kw) -> float:
 
 def compare(n: int, seed: int, edges=EDGES, storages=("f32", "f16s"), load: float = 0.8, calib: int = 16,
             tol: float = 1e-6, cap: int = 20000, capacity: int = 256, q: int = 19, g: float = 1e-5,
-            plain: bool = True, rate: float | None = None, max_live_nodes: int | None = 2 ** 25) -> dict:
+            plain: bool = True, rate: float | None = None, max_live_nodes: int | None = 2 ** 25,
+            serial: bool = False) -> dict:
     """The serving comparison: Poisson arrivals at `load` times the batched
     FP32 capacity (measured on `calib` requests of the same stream; or at a
     given `rate`), served batched in each storage format and plain (one at a
-    time, FP32)."""
+    time, FP32). With ``serial`` the batched FP32 server also runs without
+    host/device overlap, for comparison."""
     reqs = make_requests(n, seed, edges)
     cap_rps = None
     if rate is None:
@@ -343,6 +427,16 @@ def compare(n: int, seed: int, edges=EDGES, storages=("f32", "f16s"), load: floa
             srv.batch.close()
         res[st] = r
         out[f"batched_{st}"] = summarize(r, srv.fluid_updates)
+    if serial:
+        srv = BatchedServer(q=q, storage="f32", capacity=capacity, tol=tol, cap=cap, g=g,
+                            max_live_nodes=max_live_nodes, overlap=False)
+        try:
+            r = srv.run(reqs)
+        finally:
+            srv.batch.close()
+        out["batched_f32_serial"] = summarize(r, srv.fluid_updates)
+        out["batched_f32_serial"]["max_rel_permeability_diff_vs_batched_f32"] = permeability_diff(r, res["f32"]) \
+            if "f32" in res else None
     if plain:
         rp, up = serve_plain(reqs, q=q, storage="f32", tol=tol, cap=cap, g=g)
         res["plain"] = rp
@@ -361,13 +455,14 @@ def main(argv=None) -> int:
     ap.add_argument("--calib", type=int, default=32)
     ap.add_argument("--storages", default="f32,f16s")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--serial", action="store_true", help="also run the batched FP32 server without overlap")
     ap.add_argument("--rate", type=float, default=None, help="arrival rate (1/s) instead of calibrating")
     ap.add_argument("--max-live-nodes", type=int, default=2 ** 25, help="cap on live box nodes (0: none)")
     ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)
     edges = tuple(e for e in EDGES if e <= a.max_edge)
     res = compare(a.requests, a.seed, edges, tuple(a.storages.split(",")), a.load, a.calib, plain=not a.no_plain,
-                  rate=a.rate, max_live_nodes=a.max_live_nodes or None)
+                  rate=a.rate, max_live_nodes=a.max_live_nodes or None, serial=a.serial)
     line = json.dumps(res)
     print(line)
     if a.out:

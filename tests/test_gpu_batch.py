@@ -219,3 +219,31 @@ def test_poisoned_box_does_not_touch_its_neighbours():
         mixed = B.get_fields(s)
     for a, b in zip(alone, mixed):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("storage", ("f32", "f16s"))
+def test_queued_stats_equal_stats(storage):
+    """Statistics queued behind the steps (stats_queue) and taken later
+    (stats_wait) equal the synchronous ones of the same moment, whatever is
+    queued in between: more steps, the release of a box, an admission."""
+    from paper_2312_14742_gb300 import lbm
+    bx = boxes(23)
+    with Batch(19, storage, capacity=6, graph_steps=50) as B:
+        slots = [B.admit(s, per, g) for s, per, g in bx[:3]]
+        B.step(150)
+        ref = B.stats(slots, allow_diverged=True)
+        B.stats_queue(slots)
+        assert lbm.lbm_tau1_batch_stats_queue(B.b, 0, None) == lbm.LBM_ESTATE  # one request at a time
+        B.step(100)
+        B.release(slots[1])
+        extra = B.admit(*bx[3])
+        got = B.stats_wait(allow_diverged=True)
+        assert got == ref
+        assert all(r["step"] == 150 for r in got)
+        later = B.stats([slots[0], slots[2]], allow_diverged=True)
+        assert [r["step"] for r in later] == [250, 250] and later[0] != ref[0]
+        assert lbm.lbm_tau1_batch_stats_wait(B.b, None) == lbm.LBM_ESTATE  # nothing queued
+        B.stats_queue([slots[0], extra])
+        B.step(50)
+        got = B.stats_wait(allow_diverged=True)
+        assert [r["step"] for r in got] == [250, 0]

@@ -35,16 +35,19 @@ def plain(requests):
     return {r.id: r for r in res}
 
 
-def run_batched(reqs, storage, capacity=8):
-    srv = serve.BatchedServer(storage=storage, capacity=capacity, tol=1e-6, cap=4000)
+def run_batched(reqs, storage, capacity=8, overlap=True):
+    srv = serve.BatchedServer(storage=storage, capacity=capacity, tol=1e-6, cap=4000, overlap=overlap)
     try:
         return {r.id: r for r in srv.run(reqs)}, srv
     finally:
         srv.batch.close()
 
 
-def test_batched_fp32_equals_plain(requests, plain):
-    got, srv = run_batched(requests, "f32")
+@pytest.mark.parametrize("overlap", (True, False))
+def test_batched_fp32_equals_plain(requests, plain, overlap):
+    """With and without host/device overlap (statistics taken while the next
+    chunk runs)."""
+    got, srv = run_batched(requests, "f32", overlap=overlap)
     assert sorted(got) == sorted(plain)
     for i, r in got.items():
         assert r.status == plain[i].status

@@ -39,6 +39,7 @@ class FakeBatch:
         self.live_boxes = {}
         self.next_slot = 0
         self.admit_order = []
+        self.released_steps = {}
         self.reqs = {(r.edge, r.seed): r for r in requests}
 
     def admit(self, mask, periodic, g):
@@ -68,9 +69,18 @@ class FakeBatch:
                         "permeability": serve.NU * U / 1e-5, "step": steps})
         return out
 
+    def stats_queue(self, slots):
+        # the fake steps synchronously: the statistics stand as of now
+        self._queued = self.stats(slots, True)
+
+    def stats_wait(self, allow_diverged=False):
+        out, self._queued = self._queued, None
+        return out
+
     def release(self, s):
-        req, _ = self.live_boxes.pop(s)
+        req, steps = self.live_boxes.pop(s)
         self.used -= req.edge ** 3
+        self.released_steps[req.id] = steps
 
     @property
     def live(self):
@@ -154,6 +164,32 @@ def test_batched_server_fifo_budget_and_latency():
     summ = serve.summarize(res, srv.fluid_updates)
     assert summ["requests"] == 40 and summ["status"]["converged"] == 40
     assert summ["p99_latency_s"] >= summ["p50_latency_s"] > 0
+
+
+def test_overlap_gives_the_serial_answers():
+    """The overlapped server admits while a chunk runs and takes the chunk's
+    statistics afterwards: every request gets the same steps, status and
+    permeability as with the serial server, and no box is stepped past the
+    chunk that answered it."""
+    reqs = serve.make_requests(25, 55, edges=(32, 48, 64))
+    arr = serve.poisson_arrivals(25, 40.0, 55)
+    for r, a in zip(reqs, arr):
+        r.arrival = float(a)
+    out = {}
+    for overlap in (False, True):
+        clock = FakeClock()
+        fb = FakeBatch(clock, 4 * 64 ** 3, reqs)
+        srv = serve.BatchedServer(batch=fb, clock=clock, sleep=clock.sleep, overlap=overlap)
+        res = {r.id: r for r in srv.run(reqs, geometry_fn=fake_geometry, workers=0)}
+        assert len(res) == 25 and fb.live == 0 and fb.used == 0
+        assert fb.admit_order == [r.id for r in sorted(reqs, key=lambda r: (r.arrival, r.id))]
+        for i, r in res.items():
+            assert fb.released_steps[i] == r.steps
+        out[overlap] = (res, srv.fluid_updates)
+    ser, ovl = out[False][0], out[True][0]
+    for i in ser:
+        assert (ser[i].steps, ser[i].status, ser[i].permeability) == (ovl[i].steps, ovl[i].status, ovl[i].permeability)
+    assert out[True][1] == out[False][1] == sum(r.n_fluid * r.steps for r in ser.values())
 
 
 def test_request_larger_than_the_budget_is_an_error():
