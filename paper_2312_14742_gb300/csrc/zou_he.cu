@@ -19,9 +19,10 @@
 // stream, reads the same pre state, and overwrites the face nodes of the post
 // state. One thread per face node; a block first evaluates the moments of
 // every source node of its 32 x 8 patch of the face once, into shared memory.
-// The face arithmetic is FP64 for every storage format: u is the difference
-// of two sums of about rho_b - 1 each, and the faces are a small share of the
-// nodes.
+// The known populations are evaluated as the step kernels evaluate them, in
+// the storage format's compute precision (FP32 for FP32 and 16-bit storage);
+// their weighted sums and the face velocity are FP64, because u is the
+// difference of two sums of about rho_b - 1 each.
 #include "kernels.h"
 #include "static_for.cuh"
 #include "tau1_node.cuh"
@@ -35,8 +36,8 @@ namespace {
 // the sources of every known population.
 constexpr int FU = 32, FV = 8, SU = FU + 2, SV = FV + 2;
 
-struct FaceMoments {
-    double A[2][SV][SU], Px[2][SV][SU], Py[2][SV][SU], Pz[2][SV][SU], H[2][SV][SU];
+template <typename L> struct FaceMoments {
+    L A[2][SV][SU], Px[2][SV][SU], Py[2][SV][SU], Pz[2][SV][SU], H[2][SV][SU];
     unsigned char wall[2][SV][SU];  // outside a non-periodic face, or solid
 };
 
@@ -65,10 +66,10 @@ __global__ void __launch_bounds__(FU * FV) zou_he_kernel(StepArgs a, int axis, d
                                                           int tiles_v)
 {
     using S = Storage<ST>;
-    using C = typename S::ctype;  // stored values
-    using T = double;             // face arithmetic
+    using C = typename S::ctype;  // stored values, and the arithmetic of the known populations
+    using T = double;             // their sums and the face velocity
     using LT = Lat<Q>;
-    __shared__ FaceMoments fm;
+    __shared__ FaceMoments<C> fm;
     // sizes and periodicity along the face axis and the in-face axes u, v
     const int na = axis == 0 ? a.nx : (axis == 1 ? a.ny : a.nz);
     const int nu = axis == 0 ? a.ny : a.nx;
@@ -83,8 +84,7 @@ __global__ void __launch_bounds__(FU * FV) zou_he_kernel(StepArgs a, int axis, d
     const int sgn = side ? -1 : 1;
     const int pa = side ? na - 1 : 0;
     const Scales sc(a.dscale);
-    // the step kernels evaluate g in the compute precision of the format
-    const T gx = (T)gcomp<C>(a, 0), gy = (T)gcomp<C>(a, 1), gz = (T)gcomp<C>(a, 2);
+    const C gx = gcomp<C>(a, 0), gy = gcomp<C>(a, 1), gz = gcomp<C>(a, 2);
 
     // every source node's moments, once per block (the face axis is not
     // periodic: the inner plane lies outside only when the box is one plane)
@@ -97,12 +97,12 @@ __global__ void __launch_bounds__(FU * FV) zou_he_kernel(StepArgs a, int axis, d
         const bool near = cu <= nu && cv <= nv;
         const bool inside = near && ca >= 0 && ca < na && wrap_axis(cu, nu, per_u) && wrap_axis(cv, nv, per_v);
         bool wall = !inside;
-        NodeMoments<T> m{T(0), T(0), T(0), T(0), T(0)};
+        NodeMoments<C> m{C(0), C(0), C(0), C(0), C(0)};
         if (inside) {
             C e0, e1, e2, e3;
             S::load(a.pre, face_node(a, axis, ca, cu, cv), sc.inv, e0, e1, e2, e3);
             wall = isnan(e0);
-            if (!wall) m = node_moments<T>((T)e0, (T)e1, (T)e2, (T)e3, gx, gy, gz);
+            if (!wall) m = node_moments<C>(e0, e1, e2, e3, gx, gy, gz);
         }
         fm.A[j][sv][su] = m.A;
         fm.Px[j][sv][su] = m.Px;
@@ -117,13 +117,13 @@ __global__ void __launch_bounds__(FU * FV) zou_he_kernel(StepArgs a, int axis, d
     if (u0 + tu >= nu || v0 + tv >= nv) return;
     if (fm.wall[0][tv + 1][tu + 1]) return;  // solid face node
     const uint32_t i = face_node(a, axis, pa, u0 + tu, v0 + tv);
-    NodeMoments<T> own;
+    NodeMoments<C> own;
     own.A = fm.A[0][tv + 1][tu + 1];
     own.Px = fm.Px[0][tv + 1][tu + 1];
     own.Py = fm.Py[0][tv + 1][tu + 1];
     own.Pz = fm.Pz[0][tv + 1][tu + 1];
     own.H = fm.H[0][tv + 1][tu + 1];
-    T h0 = T(LT::w(0)) * own.A, hout = T(0);  // rest: the node's own equilibrium
+    T h0 = T(LT::w(0)) * T(own.A), hout = T(0);  // rest: the node's own equilibrium
     static_for<1, Q>([&](auto kc) {
         constexpr int K = decltype(kc)::value;
         constexpr int cx = LT::c(K, 0), cy = LT::c(K, 1), cz = LT::c(K, 2);
@@ -132,17 +132,17 @@ __global__ void __launch_bounds__(FU * FV) zou_he_kernel(StepArgs a, int axis, d
         // source x - c_K: the face plane (c_K along the axis 0) or the inner plane
         const int j = ck == 0 ? 0 : 1;
         const int su = tu + 1 - (axis == 0 ? cy : cx), sv = tv + 1 - (axis == 2 ? cy : cz);
-        T v;
+        C vc;
         if (fm.wall[j][sv][su]) {
             // halfway bounce-back: own previous state in direction inv(K), p(inv K) = -p(K)
-            const T p = T(cx) * own.Px + T(cy) * own.Py + T(cz) * own.Pz;
-            v = feq_scaled(own.A, own.H, -p);
+            const C p = C(cx) * own.Px + C(cy) * own.Py + C(cz) * own.Pz;
+            vc = feq_scaled(own.A, own.H, -p);
         } else {
-            const T Px = fm.Px[j][sv][su], Py = fm.Py[j][sv][su], Pz = fm.Pz[j][sv][su];
-            const T p = T(cx) * Px + T(cy) * Py + T(cz) * Pz;
-            v = feq_scaled(fm.A[j][sv][su], fm.H[j][sv][su], p);
+            const C Px = fm.Px[j][sv][su], Py = fm.Py[j][sv][su], Pz = fm.Pz[j][sv][su];
+            const C p = C(cx) * Px + C(cy) * Py + C(cz) * Pz;
+            vc = feq_scaled(fm.A[j][sv][su], fm.H[j][sv][su], p);
         }
-        v = T(LT::w(K)) * v;
+        const T v = T(LT::w(K)) * T(vc);
         if (ck == 0) h0 += v;
         else hout += v;
     });
