@@ -66,7 +66,8 @@ __host__ __device__ constexpr int dx_of(int j) { return j == 0 ? 0 : (j == 1 ? 1
 //   Seam s in [0, W], side UP (values with c_y = +1 from row y0 + 2s - 1) and
 //   DN (c_y = -1 from row y0 + 2s), each: sigma[34], then per x slot j and c_z
 //   index a value row [34]; position x' + 1 for x' in [-1, 32].
-//   XH[w][side]: the halo column of warp w (side 0: x0 - 1, 1: x0 + 32):
+//   XH[w][side]: the halo column of warp w (side 0: x0 - 1, 1: x0 + 32; w = W
+//   is written by the corner lanes and read by nobody):
 //   [0, 6) c_y = 0 values, lanes (A, B) per c_z; [6, 8) sigma (A, B);
 //   [8, 8 + n) c_y = +1 values of row A; [8 + n, 8 + 2n) c_y = -1 values of row B.
 template <int Q, int W, typename E> struct RCfg {
@@ -80,7 +81,7 @@ template <int Q, int W, typename E> struct RCfg {
     static constexpr int NXY = nzv<Q>(1, 1);  // c_z values of an in-plane diagonal
     static constexpr int XHW = 16;
     static constexpr int XH0 = (W + 1) * 2 * SIDE;
-    static constexpr int SLOT = XH0 + W * 2 * XHW;
+    static constexpr int SLOT = XH0 + (W + 1) * 2 * XHW;  // XH of warp W: the corners' spare
     static constexpr size_t SLOT_BYTES = ((size_t)SLOT * sizeof(E) + 127) / 128 * 128;
     static_assert(8 + 2 * NXY <= XHW, "halo column entry");
 };
@@ -294,7 +295,10 @@ __device__ __forceinline__ void rowpair_column(const StepArgs& a, const Scales& 
                 const L pa = m.Px * L(E(hc_right ? -1 : 1));
                 const L pb = m.Py;
                 const L pp = pa + pb, pm = pa - pb;
-                E* x = xh(sl, hc_w, hc_right ? 1 : 0);
+                // a corner lane writes its halo-column entries to the spare slot
+                // of warp W (read by nobody), so that corner and regular lanes
+                // run the same instructions
+                E* x = xh(sl, hc_corner ? W : hc_w, hc_right ? 1 : 0);
                 // seam targets: a regular lane's row A (c_y = -1) goes to seam hc_w DN
                 // and its row B (c_y = +1) to seam hc_w + 1 UP; a corner lane's row A
                 // (y0 - 1, c_y = +1) to seam 0 UP and row B (y0 + 2W, c_y = -1) to seam W DN
@@ -302,30 +306,24 @@ __device__ __forceinline__ void rowpair_column(const StepArgs& a, const Scales& 
                 E* sB = hc_corner ? side(sl, W, 1) : side(sl, hc_w + 1, 0);
                 sA[pos] = hs.v.x;
                 sB[pos] = hs.v.y;
-                if (!hc_corner) {
-                    x[6] = hs.v.x;
-                    x[7] = hs.v.y;
-                }
+                x[6] = hs.v.x;
+                x[7] = hs.v.y;
                 static_for<0, 3>([&](auto cc) {
                     constexpr int cz = decltype(cc)::value - 1;
                     auto zt = [&](L pv) { return cz == 0 ? pv : (cz > 0 ? pv + m.Pz : pv - m.Pz); };
                     const L v0 = f(zt(pa));
-                    if (!hc_corner) {
-                        x[2 * (cz + 1)] = v0.v.x;
-                        x[2 * (cz + 1) + 1] = v0.v.y;
-                    }
+                    x[2 * (cz + 1)] = v0.v.x;
+                    x[2 * (cz + 1) + 1] = v0.v.y;
                     if constexpr (NXY == 3 || cz == 0) {
                         constexpr int ci = czi<Q>(1, 1, cz);
                         const L vp = f(zt(pp)), vm = f(zt(pm));
-                        if (hc_corner) {
-                            sA[C::voff(j, ci) + pos] = vp.v.x;  // (y0 - 1): c_y = +1
-                            sB[C::voff(j, ci) + pos] = vm.v.y;  // (y0 + 2W): c_y = -1
-                        } else {
-                            sA[C::voff(j, ci) + pos] = vm.v.x;  // row A: c_y = -1
-                            sB[C::voff(j, ci) + pos] = vp.v.y;  // row B: c_y = +1
-                            x[8 + ci] = vp.v.x;                 // row A, c_y = +1: for row B of lane 0/31
-                            x[8 + NXY + ci] = vm.v.y;           // row B, c_y = -1: for row A of lane 0/31
-                        }
+                        // a corner's row A (y0 - 1) sends c_y = +1, its row B
+                        // (y0 + 2W) c_y = -1; a regular row A sends c_y = -1 and
+                        // row B c_y = +1 across the seams
+                        sA[C::voff(j, ci) + pos] = hc_corner ? vp.v.x : vm.v.x;
+                        sB[C::voff(j, ci) + pos] = hc_corner ? vm.v.y : vp.v.y;
+                        x[8 + ci] = vp.v.x;        // row A, c_y = +1: for row B of lane 0/31
+                        x[8 + NXY + ci] = vm.v.y;  // row B, c_y = -1: for row A of lane 0/31
                     }
                 });
             }
