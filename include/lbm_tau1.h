@@ -256,6 +256,15 @@ lbm_status lbm_tau1_autotune(lbm_tau1* h, int32_t trials, int32_t* chosen, float
  * cache off (the default). The file is read and rewritten on each use. */
 void lbm_tau1_set_tune_cache(const char* path);
 
+/* Self-test of the failure detection (no counterpart in the paper): queues
+ * on the handle's stream one warp that waits, with the staged kernels'
+ * bounded wait (about one second), on an mbarrier phase that nothing
+ * completes, and counts the timeout in the handle's counter, as a staged
+ * copy that never lands would. The next lbm_tau1_synchronize or
+ * lbm_tau1_reduce then returns LBM_ETIMEOUT (and clears the count); nothing
+ * faults and the context stays usable. For tests and health checks. */
+lbm_status lbm_tau1_selftest_timeout(lbm_tau1* h);
+
 /* Compact layout (LBM_COMPACT): how set_geometry split the box. */
 typedef struct lbm_tau1_compact_info {
     double threshold;        /* f*: fluid fraction from which a tile column is tiled */
@@ -352,6 +361,12 @@ lbm_status lbm_tau1_batch_stats(lbm_tau1_batch* b, int32_t n, const int32_t* slo
  * a time: LBM_ESTATE if one is already waiting. Errors: LBM_EINVAL (bad
  * arguments, slot not live), LBM_ECUDA. */
 lbm_status lbm_tau1_batch_stats_queue(lbm_tau1_batch* b, int32_t n, const int32_t* slots);
+
+/* The self-test of lbm_tau1_selftest_timeout on the batch's stream and
+ * counter: the next lbm_tau1_batch_synchronize, lbm_tau1_batch_stats or
+ * lbm_tau1_batch_stats_wait (of statistics queued after it) returns
+ * LBM_ETIMEOUT. */
+lbm_status lbm_tau1_batch_selftest_timeout(lbm_tau1_batch* b);
 
 /* Waits for the statistics queued by lbm_tau1_batch_stats_queue and fills
  * out[0..n-1] (n as queued). Returns LBM_EDIVERGED, with every out[] filled,

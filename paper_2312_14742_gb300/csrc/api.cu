@@ -845,6 +845,14 @@ lbm_status lbm_tau1_set_variant(lbm_tau1* h, int32_t variant)
     return (h->compact && h->has_geometry) ? build_compact(h) : LBM_OK;
 }
 
+lbm_status lbm_tau1_selftest_timeout(lbm_tau1* h)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "selftest_timeout: NULL handle");
+    LBM_CUDA(h, launch_selftest_timeout(h->dtimeouts, h->stream), "selftest_timeout: launch");
+    ++h->launches;
+    return LBM_OK;
+}
+
 lbm_status lbm_tau1_set_compact_threshold(lbm_tau1* h, double f)
 {
     if (!h) return fail(nullptr, LBM_EINVAL, "set_compact_threshold: NULL handle");

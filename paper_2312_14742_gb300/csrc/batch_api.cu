@@ -587,6 +587,14 @@ lbm_status lbm_tau1_batch_stats(lbm_tau1_batch* b, int32_t n, const int32_t* slo
     return LBM_OK;
 }
 
+lbm_status lbm_tau1_batch_selftest_timeout(lbm_tau1_batch* b)
+{
+    if (!b) return bfail(nullptr, LBM_EINVAL, "batch_selftest_timeout: NULL batch");
+    BCUDA(b, launch_selftest_timeout(b->dtimeouts, b->stream), "batch_selftest_timeout: launch");
+    ++b->launches;
+    return LBM_OK;
+}
+
 lbm_status lbm_tau1_batch_stats_queue(lbm_tau1_batch* b, int32_t n, const int32_t* slots)
 {
     if (!b) return bfail(nullptr, LBM_EINVAL, "batch_stats_queue: NULL batch");

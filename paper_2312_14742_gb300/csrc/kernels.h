@@ -32,6 +32,10 @@ cudaError_t launch_tau1_rowpair(int q, int storage, int shape, int zchunk, const
 int tau1_rowpair_tile_height(int q, int storage, int shape);
 cudaError_t launch_tau1_rowpair_list(int q, int storage, int shape, int zchunk, const StepArgs& a, const int* list,
                                      int count, cudaStream_t s);
+// Self-test (selftest.cu): one warp waits, bounded, on an mbarrier phase
+// that nothing completes and counts the timeout in *timeouts.
+cudaError_t launch_selftest_timeout(unsigned int* timeouts, cudaStream_t s);
+
 // Compact porous layout (compact.cu): tile columns of 32 x h x zchunk nodes,
 // the unit of the row-pair variant (shape, zchunk) (variant v of
 // [0, 2 tau1_rowpair_shapes): shape v mod R, zchunk 24 below R, else 32),

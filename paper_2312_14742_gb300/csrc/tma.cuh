@@ -4,9 +4,10 @@
 // One thread issues a tiled 3D bulk copy of a box of the state into shared
 // memory; the copy reports its bytes to an mbarrier of that buffer, and every
 // thread waits for the barrier's phase before reading the box. Waits are
-// bounded: a wait that runs past its limit counts a timeout in
-// g_tma_timeouts (read by the host) and lets the thread go on, so that a
-// missing completion can never hang the GPU.
+// bounded: a wait that runs past its limit returns false; the kernel then
+// counts a timeout in its caller's device counter (StepArgs::timeouts, read
+// and cleared by the host, which reports LBM_ETIMEOUT), stops issuing copies
+// and storing, so that a missing completion can never hang the GPU.
 #pragma once
 
 #include <cstdint>

@@ -92,6 +92,8 @@ SIGNATURES = {
     "lbm_tau1_launch_count": (_I64, [_H]),
     "lbm_tau1_set_pressure": (_I, [_H, ctypes.c_int32, ctypes.c_double, ctypes.c_double]),
     "lbm_tau1_copy_plane": (_I, [_H, ctypes.c_int32, _P, ctypes.c_int32]),
+    "lbm_tau1_selftest_timeout": (_I, [_H]),
+    "lbm_tau1_batch_selftest_timeout": (_I, [_H]),
     "lbm_tau1_set_compact_threshold": (_I, [_H, ctypes.c_double]),
     "lbm_tau1_get_compact_info": (_I, [_H, ctypes.POINTER(lbm_tau1_compact_info)]),
     "lbm_tau1_variant_count": (ctypes.c_int32, [_H]),
@@ -203,6 +205,14 @@ def lbm_tau1_set_pressure(h, axis: int, rho_lo: float, rho_hi: float) -> int:
 
 def lbm_tau1_copy_plane(h, z: int, buf, to_handle: int) -> int:
     return _fn("lbm_tau1_copy_plane")(h, z, buf, to_handle)
+
+
+def lbm_tau1_selftest_timeout(h) -> int:
+    return _fn("lbm_tau1_selftest_timeout")(h)
+
+
+def lbm_tau1_batch_selftest_timeout(b) -> int:
+    return _fn("lbm_tau1_batch_selftest_timeout")(b)
 
 
 def lbm_tau1_set_compact_threshold(h, f: float) -> int:
