@@ -1,5 +1,6 @@
 """Timings of the paths beside the 3D dense step: the D2Q9 kernels, the
-constant-density (Zou-He) faces and a z-slab split on one GPU.
+constant-density (Zou-He) faces, the compact layout's node-list kernel and a
+z-slab split on one GPU.
 
 - D2Q9 (Section 3.1) on the paper's large 2D geometry, a 4000 x 4000 plane
   (Section 4): a channel with solid rows y = 0 and y = ny - 1, periodic in x,
@@ -10,6 +11,9 @@ constant-density (Zou-He) faces and a z-slab split on one GPU.
 - Constant-density faces (Section 3.3's rho_in / rho_out) on x: the step plus
   the face kernel, against the same box stepped with periodic x and a body
   force. D2Q9 on the 4000^2 channel; D3Q19 on the 256^3 porous bench box.
+- compact layout (Section 4.3's porous media, Section 5's indirect
+  addressing) on a 256^3 medium of porosity 0.2: the node-list kernel alone
+  (f* = 1.01) and the autotuned split.
 - z-slab (one halo plane exchanged per step, Section 2.1.2's independence of
   the nodes within a step): the 256^3 bench box as two slabs on one GPU,
   exchanged through the C ABI (lbm_tau1_copy_plane) before every step, against
@@ -19,7 +23,7 @@ constant-density (Zou-He) faces and a z-slab split on one GPU.
 CUDA events on the launching stream, after warm-up. Prints one JSON object
 per line.
 
-Usage: python -m paper_2312_14742_gb300.rows_bench [--steps 200] [--out FILE]
+Usage: python -m paper_2312_14742_gb300.rows_bench [--steps 200] [--rows d2q9,faces,slab,compact] [--out FILE]
 """
 from __future__ import annotations
 
@@ -119,14 +123,44 @@ def slab_rows(n: int, steps: int, warmup: int, stream) -> list[dict]:
              "exchange_bytes_per_step": 2 * 2 * n * n * 16}]
 
 
+def compact_rows(n: int, steps: int, warmup: int, stream, peak: float) -> list[dict]:
+    """The compact layout on a low-porosity medium (256^3 by default, spheres
+    of radius 12 to porosity 0.2, the sweep's first medium at a smaller size):
+    every fluid node through the node list (f* = 1.01: the list kernel alone),
+    then the autotuned split."""
+    import lbm_inputs
+    from .lbm import LBM_COMPACT, Tau1
+
+    solid, _ = lbm_inputs.sphere_pack(n, n, n, 12.0, 0.2, lbm_inputs.workload_seed(3, 0))
+    nf = int(np.count_nonzero(solid == 0))
+    out = []
+    for name in ("list", "tuned"):
+        with Tau1(19, (n, n, n), storage="f32", g=(1e-5, 0, 0), layout=LBM_COMPACT, stream=stream) as t:
+            if name == "list":
+                t.set_compact_threshold(1.01)
+            t.set_geometry(solid)
+            if name == "tuned":
+                t.autotune(10)
+            dt = _time(t.step, steps, warmup, stream)
+            ci = t.compact_info()
+        algo = 32 * nf + ci["tiled_nodes"] + 4 * ci["listed_nodes"]
+        out.append({"row": "compact", "split": name, "size": [n, n, n], "porosity": 1.0 - float(solid.mean()),
+                    "n_fluid": nf, "ms_per_step": dt * 1e3, "gflups": nf / dt / 1e9,
+                    "algorithmic_bytes_per_step": algo, "achieved_GBps": algo / dt / 1e9,
+                    "frac_of_peak": algo / dt / 1e9 / peak, "compact": ci})
+    return out
+
+
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--n2", type=int, default=4000, help="edge of the D2Q9 plane")
     ap.add_argument("--n3", type=int, default=256, help="edge of the 3D box")
+    ap.add_argument("--rows", default="d2q9,faces,slab,compact", help="which rows to time")
     ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)
+    which = set(a.rows.split(","))
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     sys.path.insert(0, root)
     import torch
@@ -138,8 +172,16 @@ def main(argv=None) -> int:
     peak, kind = (float(json.load(open(pk))["hbm_gbs"]), "measured") if os.path.exists(pk) else (6800.0, "fallback")
     stream = torch.cuda.current_stream()
     rows = []
-    for r in (d2q9_rows(a.n2, a.steps, a.warmup, stream, peak) + face_rows(a.n2, a.n3, a.steps, a.warmup, stream)
-              + slab_rows(a.n3, a.steps, a.warmup, stream)):
+    todo = []
+    if "compact" in which:
+        todo += compact_rows(a.n3, a.steps, a.warmup, stream, peak)
+    if "d2q9" in which:
+        todo += d2q9_rows(a.n2, a.steps, a.warmup, stream, peak)
+    if "faces" in which:
+        todo += face_rows(a.n2, a.n3, a.steps, a.warmup, stream)
+    if "slab" in which:
+        todo += slab_rows(a.n3, a.steps, a.warmup, stream)
+    for r in todo:
         r["peak_GBps"] = peak
         r["peak_kind"] = kind
         rows.append(r)
