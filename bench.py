@@ -41,7 +41,9 @@ def parse():
     p.add_argument("--steps", type=int, default=1000)
     p.add_argument("--warmup", type=int, default=2000)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--q", type=int, default=19)
+    p.add_argument("--q", type=int, default=19, choices=[9, 19, 27],
+                   help="lattice; 9 (D2Q9) steps a size x size channel, the paper's 2D case")
+    p.add_argument("--layout", default="dense", choices=["dense", "sparse", "compact"])
     p.add_argument("--storage", default="f32")
     p.add_argument("--kernel", default="auto")
     p.add_argument("--variant", type=int, default=-1,
@@ -127,21 +129,32 @@ class ClockSampler:
 
 def workload(args):
     n = args.size
+    if args.q == 9:
+        # the paper's 2D geometry (Section 3.3, Section 4): a channel, solid rows y = 0 and n - 1
+        solid = np.zeros((1, n, n), np.uint8)
+        solid[0, 0] = 1
+        solid[0, n - 1] = 1
+        info = argparse.Namespace(porosity=float(np.mean(solid == 0)), spheres=0)
+        return solid, info
     seed = lbm_inputs.workload_seed(WORKLOAD_INDEX, 0)
     solid, info = lbm_inputs.sphere_pack(n, n, n, args.radius, args.porosity, seed)
     return solid, info
 
 
 def workload_name(args, info):
-    return (f"D3Q{args.q} Tau1 {args.storage} dense, {args.size}^3 periodic, overlapping spheres r={args.radius:g} "
-            f"to porosity {args.porosity:g} (reached {info.porosity:.4f}, {info.spheres} spheres), "
+    if args.q == 9:
+        return (f"D2Q9 Tau1 {args.storage} {args.layout}, {args.size} x {args.size} channel (solid rows y = 0 and "
+                f"{args.size - 1}), periodic, g_x={args.gx:g}")
+    return (f"D3Q{args.q} Tau1 {args.storage} {args.layout}, {args.size}^3 periodic, overlapping spheres "
+            f"r={args.radius:g} to porosity {args.porosity:g} (reached {info.porosity:.4f}, {info.spheres} spheres), "
             f"g_x={args.gx:g}")
 
 
-def bytes_per_fluid_node(storage: str) -> int:
+def bytes_per_fluid_node(storage: str, q: int = 19) -> int:
     # 2 (d+1) s: one read and one write of (rho, u) per fluid node (Section 2.1.3)
     s = {"f64": 8, "f32": 4, "f16s": 2, "bf16s": 2}[storage]
-    return 2 * 4 * s
+    d = 2 if q == 9 else 3
+    return 2 * (d + 1) * s
 
 
 TILED_KERNEL_SOURCES = ("tau1_tiled.cu", "tau1_tiled_tma.cu", "tau1_rowpair.cu", "rowpair.cuh", "tile_column.cuh",
@@ -170,7 +183,7 @@ def ncu_traffic(args):
     """DRAM bytes per launch from the committed ncu summary of this workload,
     if it was taken on the current kernel sources."""
     p = os.path.join(ROOT, "profiles", f"tau1_d3q{args.q}_{args.storage}_{args.size}_traffic.json")
-    if not os.path.exists(p):
+    if args.layout != "dense" or args.q == 9 or not os.path.exists(p):
         return None
     d = json.load(open(p))
     if d.get("kernel_source_hash") != kernel_source_hash():
@@ -198,8 +211,11 @@ def cpu_baseline(args, solid, nsteps):
     for _ in range(nsteps):
         st = D.tau1_step(st)
     dt = time.perf_counter() - t0
-    return {"value": nf * nsteps / dt / 1e9, "unit": "GFLUPS", "cores": oracle.get_threads(), "kind": "oracle",
-            "sample": f"{nsteps} FP64 oracle steps of the full {args.size}^3 box, OpenMP over z"}
+    nz = solid.shape[0]
+    box = f"{args.size} x {args.size} plane" if args.q == 9 else f"{args.size}^3 box"
+    # the oracle's threads share the z planes: a plane (nz = 1) runs on one
+    return {"value": nf * nsteps / dt / 1e9, "unit": "GFLUPS", "cores": min(oracle.get_threads(), nz),
+            "kind": "oracle", "sample": f"{nsteps} FP64 oracle steps of the full {box}, OpenMP over z"}
 
 
 # ---------------------------------------------------------------------------
@@ -243,8 +259,8 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_name(args, info)},
-            "cpu_baseline": {"value": v, "unit": "GFLUPS", "cores": oracle.get_threads(), "kind": "oracle",
-                             "sample": desc},
+            "cpu_baseline": {"value": v, "unit": "GFLUPS", "cores": min(oracle.get_threads(), planes),
+                             "kind": "oracle", "sample": desc},
             "e2e": {"value": v, "unit": "GFLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -277,7 +293,7 @@ def run_ours(args):
         torch.cuda.synchronize(dev)
 
     t = Tau1(args.q, (nx, ny, nz), storage=args.storage, periodic=(1, 1, 1), g=(args.gx, 0, 0),
-             kernel=args.kernel, stream=stream)
+             kernel=args.kernel, stream=stream, layout=args.layout)
     t.set_geometry(solid)
     t.step(min(args.warmup, 50))
     if args.variant >= 0:
@@ -330,7 +346,7 @@ def run_ours(args):
 
     # comparator: standard BGK at tau = 1 with stored populations, same box
     bgk = None
-    if not args.no_bgk and args.storage in ("f32", "f64"):
+    if not args.no_bgk and args.storage in ("f32", "f64") and args.q != 9 and args.layout == "dense":
         from paper_2312_14742_gb300.lbm import LBM_SCHEME_BGK
         tb = Tau1(args.q, (nx, ny, nz), storage=args.storage, periodic=(1, 1, 1), g=(args.gx, 0, 0),
                   stream=stream, scheme=LBM_SCHEME_BGK)
@@ -361,7 +377,7 @@ def run_ours(args):
 
     # serving: Poisson permeability requests, continuously batched vs one at a time (rank 0)
     serve_out = None
-    if rank == 0 and not args.no_serve:
+    if rank == 0 and not args.no_serve and args.q != 9:
         from paper_2312_14742_gb300 import serve
         edges = tuple(e for e in serve.EDGES if e <= args.serve_max_edge)
         serve_out = serve.compare(args.serve_requests, lbm_inputs.workload_seed(SERVE_INDEX, 0), edges,
@@ -373,7 +389,7 @@ def run_ours(args):
         return
 
     peak, peak_kind = measured_peaks()
-    algo_bytes = bytes_per_fluid_node(args.storage) * nf + n  # + 1 B mask per node
+    algo_bytes = bytes_per_fluid_node(args.storage, args.q) * nf + n  # + 1 B mask per node
     if bgk is not None:
         bgk["tau1_over_bgk"] = (nf * args.steps / dt / 1e9) / bgk["value"]
     launch_s = dt / args.steps

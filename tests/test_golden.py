@@ -35,9 +35,9 @@ def bench_module():
 
 def test_table_complexity_is_consistent():
     t = load("tab_complexity.json")
-    for lat, q in (("D3Q19", 19), ("D3Q27", 27)):
+    for lat, q, d in (("D2Q9", 9, 2), ("D3Q19", 19, 3), ("D3Q27", 27, 3)):
         assert t["lbm"][lat]["AB"] == 2 * q and t["lbm"][lat]["traffic"] == 2 * q
-        assert t["tau1"][lat]["traffic"] == 2 * (3 + 1)
+        assert t["tau1"][lat]["traffic"] == 2 * (d + 1)
         assert t["tau1"][lat]["traffic_reduction"] == t["lbm"][lat]["traffic"] / t["tau1"][lat]["traffic"]
 
 
@@ -46,6 +46,8 @@ def test_bench_bytes_match_the_table(storage, s):
     t = load("tab_complexity.json")
     b = bench_module()
     assert b.bytes_per_fluid_node(storage) == t["tau1"]["D3Q19"]["traffic"] * s
+    assert b.bytes_per_fluid_node(storage, 27) == t["tau1"]["D3Q27"]["traffic"] * s
+    assert b.bytes_per_fluid_node(storage, 9) == t["tau1"]["D2Q9"]["traffic"] * s
 
 
 @pytest.mark.parametrize("storage,s", (("f64", 8), ("f32", 4), ("f16s", 2), ("bf16s", 2)))
