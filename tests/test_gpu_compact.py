@@ -196,3 +196,35 @@ def test_compact_threshold_rejected_out_of_range():
     with Tau1(19, (32, 8, 4)) as t:
         with pytest.raises(LbmError):
             t.set_compact_threshold(0.3)
+
+
+@pytest.mark.parametrize("dims,per", [((1, 1, 1), (1, 1, 1)), ((2, 3, 1), (1, 0, 1)), ((5, 1, 7), (0, 1, 1)),
+                                      ((1, 9, 4), (1, 1, 0)), ((33, 2, 3), (1, 1, 1))])
+@pytest.mark.parametrize("storage", ("f32", "f64"))
+def test_compact_degenerate_boxes(dims, per, storage):
+    """Axes one or two nodes long (the node-list kernel's division by nx and
+    nx ny, and its wrap of an axis onto itself), against the dense kernels."""
+    nx, ny, nz = dims
+    solid = lbm_inputs.random_mask(nx, ny, nz, 0.2, 7500 + nx * 7 + ny)
+    st = lbm_inputs.random_fields(solid.shape, 7501, 2e-3, 3e-3, solid)
+    g = (1e-5, -2e-6, 3e-6)
+    ref, _, _ = run(19, solid, per, g, storage, 12, st, kernel="simple")
+    got, _, info = run(19, solid, per, g, storage, 12, st, layout=LBM_COMPACT)
+    assert_same(got, ref, dims)
+    assert info["tiled_columns"] == 0 and info["listed_nodes"] == int(np.count_nonzero(solid == 0))
+
+
+@pytest.mark.parametrize("q", (19, 27))
+def test_compact_pressure_faces_match_oracle(q):
+    """Constant-density faces on z over a compact split box (tile columns of
+    both kinds), FP64 against the oracle."""
+    solid = mixed_medium(64, 16, 20, 7600 + q)
+    per = (1, 1, 0)
+    bc = (2, 1.01, 0.99)
+    D = oracle.Domain(q, solid, periodic=per, pressure=bc)
+    ref = D.tau1_run(D.zero_state(), 60)
+    got, _, info = run(q, solid, per, (0, 0, 0), "f64", 60, layout=LBM_COMPACT, thr=0.5, pressure=bc)
+    assert info["tiled_columns"] > 0 and info["listed_columns"] > 0
+    umax = max(float(np.max(np.abs(ref[a]))) for a in (1, 2, 3))
+    assert float(np.max(np.abs(got[0] - ref[0]))) <= 1e-12
+    assert max(float(np.max(np.abs(got[a] - ref[a]))) for a in (1, 2, 3)) <= 1e-12 * umax
