@@ -14,7 +14,8 @@
 // step lives in the table on the device: which copy holds a box's current
 // state, its step count (the stochastic-rounding seed), its 16-bit scales.
 // Boxes whose tiles are all full are stepped by a staged (TMA) instance of
-// the kernel through their own tensor maps (one per state copy, in device
+// the kernel (the row-pair tile column for variant 0, rowpair.cuh) through
+// their own tensor maps (one per state copy, in device
 // memory; the stage mbarriers are set up once per launch and their phases run
 // on from item to item), the others by a register instance: two work tables,
 // one launch each per step. A launch therefore has the same arguments every
@@ -30,6 +31,7 @@
 // scales chosen depend only on the box's own state and step count, so a box
 // gives the same bits alone and in any mix.
 #include "batch.h"
+#include "rowpair.cuh"
 #include "tile_column.cuh"
 
 namespace lbm {
@@ -78,17 +80,23 @@ __device__ void finish_box(BatchDomain& R, int storage)
     R.step = step;
 }
 
-template <int Q, int ST, int H, int MINB, bool TMA>
+// RP: the staged instance steps its items with the row-pair tile column
+// (rowpair_column, tile 32 x 2H: the same tiles, tensor maps and bits).
+template <int Q, int ST, int H, int MINB, bool TMA, bool RP>
 __global__ void __launch_bounds__(32 * H, MINB) tau1_batch_kernel(BatchTable* T)
 {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    // the row-pair stage buffers want 128-byte alignment
+    unsigned char* smem_raw = RP ? smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u) : smem_dyn;
     __shared__ int last;
     // FP16 only (BF16 keeps S = 1): maxima of the stored values, needed on the
     // step before each scale check
     constexpr bool AMAX = ST == ST_F16S;
     const int nitems = T->nitems, ndom = T->ndom, chunk = T->chunk;
     const int* __restrict__ begin = T->item_begin;
-    if constexpr (TMA) stage_init<Q, ST, H>(smem_raw);  // visible after the first item's barrier
+    // visible after the first item's barrier
+    if constexpr (RP) rp::rp_stage_init<Q, ST, H>(smem_raw);
+    else if constexpr (TMA) stage_init<Q, ST, H>(smem_raw);
     uint32_t phase = 0;
     __shared__ int next_item;
     // each block takes its first item by its index, then the next free one
@@ -116,7 +124,9 @@ __global__ void __launch_bounds__(32 * H, MINB) tau1_batch_kernel(BatchTable* T)
         const int x0 = (tile % R.ntx) * 32, y0 = (tile / R.ntx) * (2 * H);
         float amax[4] = {0.f, 0.f, 0.f, 0.f};
         __syncthreads();  // the previous item's last shared-memory reads are done
-        if constexpr (TMA)
+        if constexpr (RP)
+            rp::rowpair_column<Q, ST, H, AMAX>(a, sc, x0, y0, z0, z1, smem_raw, amax, T->maps + 2 * slot + c, &phase);
+        else if constexpr (TMA)
             tile_column<Q, ST, H, AMAX, true>(a, sc, x0, y0, z0, z1, smem_raw, amax, T->maps + 2 * slot + c, &phase);
         else
             tile_column<Q, ST, H, AMAX, false>(a, sc, x0, y0, z0, z1, smem_raw, amax);
@@ -154,8 +164,14 @@ struct BatchKernel {
     using E = typename Storage<ST>::ctype;
     static constexpr int H = Shape<Q, E, V>::H;
     using C = TCfg<Q, 32, H, E>;
-    static constexpr size_t SMEM = tile_smem<Q, ST, H, TMA>();
-    static constexpr auto fn() { return tau1_batch_kernel<Q, ST, H, Shape<Q, E, V>::MINB, TMA>; }
+    // variant 0 of the staged instance: the row-pair form of the same tile, at
+    // the single-box row-pair kernel's block count (a few bytes of spills in
+    // FP32 at 4 blocks: measured faster on serving mixes than 3 blocks)
+    static constexpr bool RP = TMA && V == 0 && rp::RShape<Q, E, 0>::W == H;
+    static constexpr int MINB = RP ? rp::RShape<Q, E, 0>::MINB : Shape<Q, E, V>::MINB;
+    static constexpr size_t SMEM = RP ? rp::rowpair_smem<Q, ST, H>() + 128 : tile_smem<Q, ST, H, TMA>();
+    static_assert(SMEM <= 227 * 1024, "shared memory of one block");
+    static constexpr auto fn() { return tau1_batch_kernel<Q, ST, H, MINB, TMA, RP>; }
     static cudaError_t prepare(int& grid, int& tile_h)
     {
         auto kern = fn();
