@@ -235,11 +235,25 @@ template <int ST> cudaError_t launch2(bool simple, const StepArgs& a, cudaStream
         tau1_simple2d_kernel<ST><<<grid, 256, 0, s>>>(a);
     } else {
         const int ntx = (a.nx + M2_COLS - 1) / M2_COLS;
-        // rows per warp: long enough to amortise the two halo rows, short enough
-        // to give every SM several warps
-        int chunk = 64;
+        // Rows per warp: long enough to amortise the two halo rows (about 64),
+        // and chosen so that the warps fill a whole number of waves of the
+        // warps the GPU holds at once (a last, partly filled wave leaves SMs
+        // idle while the others finish). A node's result does not depend on it.
+        auto kern = tau1_march2d_kernel<ST>;
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * M2_WARPS, 0);
+        if (e != cudaSuccess) return e;
+        const long long resident = (long long)sms * (per_sm > 0 ? per_sm : 1) * M2_WARPS;
         const long long cols = (long long)ntx;
-        while (chunk > 8 && cols * ((a.ny + chunk - 1) / chunk) < 152LL * 32) chunk /= 2;
+        const long long at64 = cols * ((a.ny + 63) / 64);
+        const long long waves = at64 / resident > 0 ? (at64 + resident / 2) / resident : 1;
+        long long rows_per_col = waves * resident / cols;  // warps per column of tiles
+        if (rows_per_col < 1) rows_per_col = 1;
+        long long chunk_l = (a.ny + rows_per_col - 1) / rows_per_col;
+        chunk_l = chunk_l < 8 ? 8 : (chunk_l > 128 ? 128 : chunk_l);
+        const int chunk = (int)chunk_l;
         const long long items = cols * ((a.ny + chunk - 1) / chunk);
         if (items > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
         const unsigned blocks = (unsigned)((items + M2_WARPS - 1) / M2_WARPS);

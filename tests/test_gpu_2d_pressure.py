@@ -84,6 +84,23 @@ def test_d2q9_march_bitwise_equals_simple(storage, dims, per):
         assert np.array_equal(a[k], b[k]), (storage, dims, k)
 
 
+@pytest.mark.parametrize("storage", ("f32", "f16s"))
+@pytest.mark.parametrize("per", [(1, 1, 1), (1, 0, 1)])
+def test_d2q9_march_bitwise_equals_simple_one_wave(storage, per):
+    """A plane large enough that the march kernel sizes its row chunks to fill
+    one wave of resident warps (3997 x 2999: 134 tile columns, a ragged last
+    column and a ragged last chunk), against the one-thread-per-node kernel."""
+    nx, ny = 3997, 2999
+    solid = plane(nx, ny, 0.25, 905)
+    st = lbm_inputs.random_fields(solid.shape, 906, 2e-3, 3e-3, solid)
+    st = (st[0], st[1], st[2], np.zeros(solid.shape))
+    g = (1e-5, 2e-6 if per[1] else 0.0, 0.0)
+    a = run(9, solid, per, g, storage, 12, state=st, kernel="simple")
+    b = run(9, solid, per, g, storage, 12, state=st, kernel="tiled")
+    for k in range(4):
+        assert np.array_equal(a[k], b[k]), (storage, per, k)
+
+
 def test_d2q9_channel_steady_exact_profile():
     """Body-force channel (solid rows y = 0 and 31): the exact discrete steady
     profile u = 3 g (y - 1/2)(30.5 - y) - g/4 of the oracle pins, on the GPU."""
