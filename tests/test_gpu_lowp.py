@@ -135,3 +135,36 @@ def test_porous_permeability_within_one_percent(storage):
     got, fgot = run_averaged(19, solid, (1, 1, 1), g, storage, steps)
     assert abs(got["permeability"] - ref["permeability"]) <= 1e-2 * abs(ref["permeability"])
     assert abs(got["max_abs_u"] - ref["max_abs_u"]) <= 2e-2 * ref["max_abs_u"]
+
+
+@pytest.mark.parametrize("storage", ("f64", "f32", "f16s", "bf16s"))
+def test_sphere_array_permeability_matches_closed_form(storage):
+    """One sphere (nodes within 6 of the centre) in a periodic 24^3 cell: a
+    simple cubic array at solid fraction 0.066. The steady permeability is
+    within 3 % of the Hasimoto / Sangani-Acrivos closed form (the oracle's
+    own pin, test_oracle_pins.sc_array_permeability, with the radius of a
+    ball of the solid nodes' volume) and, against the oracle run to the same
+    steady state, within 1e-10 (FP64), 1e-4 (FP32) or 1 % (16-bit, averaged
+    over a window)."""
+    import math
+
+    from test_oracle_pins import sc_array_permeability
+
+    L = 24
+    z, y, x = np.mgrid[0:L, 0:L, 0:L]
+    solid = (((x - 11.5) ** 2 + (y - 11.5) ** 2 + (z - 11.5) ** 2) <= 36.0).astype(np.uint8)
+    a = (3.0 * int(solid.sum()) / (4.0 * math.pi)) ** (1.0 / 3.0)
+    g = (1e-5, 0.0, 0.0)
+    ref, _, steps = oracle_to_steady(19, solid, (1, 1, 1), g, tol=1e-7)
+    if storage in ("f64", "f32"):
+        with Tau1(19, (L, L, L), storage=storage, periodic=(1, 1, 1), g=g) as t:
+            t.set_geometry(solid)
+            t.step(steps)
+            got = t.reduce()
+        tol = 1e-10 if storage == "f64" else 1e-4
+    else:
+        got, _ = run_averaged(19, solid, (1, 1, 1), g, storage, steps)
+        tol = 1e-2
+    k = got["permeability"]
+    assert abs(k - ref["permeability"]) <= tol * abs(ref["permeability"]), (storage, k, ref["permeability"])
+    assert abs(k / sc_array_permeability(L, a) - 1.0) < 0.03, (storage, k, sc_array_permeability(L, a))
