@@ -199,3 +199,41 @@ def test_low_mach_pressure_channel_matches_poiseuille():
     print(f"MAPE {mape:.4f} %, shape MAPE {shape:.4f} %, flux spread {spread:.2e}")
     assert spread <= 1e-4
     assert mape < 0.02, mape
+
+
+@pytest.mark.parametrize("storage", STORAGES)
+def test_d2q9_cylinder_array_permeability(storage):
+    """A square array of cylinders (one disc of radius 6 in a periodic 32^2
+    cell, solid fraction 0.11) driven by g_x = 1e-5 to steady state, both
+    D2Q9 kernels: permeability within 3 % of the Hasimoto / Drummond-Tahir
+    closed form (the oracle's pin) and, against the oracle run to the same
+    steady state, within 1e-10 (FP64), 1e-4 (FP32) or 1 % (16-bit, the mean
+    over a window of 20 states 50 steps apart)."""
+    import math
+
+    from oracle_steady import oracle_to_steady
+    from test_oracle_pins import sq_array_permeability
+
+    L = 32
+    y, x = np.mgrid[0:L, 0:L]
+    solid = (((x - 15.5) ** 2 + (y - 15.5) ** 2) <= 36.0).astype(np.uint8)[None]
+    a = math.sqrt(int(solid.sum()) / math.pi)
+    g = (1e-5, 0.0, 0.0)
+    ref, _, steps = oracle_to_steady(9, solid, (1, 1, 1), g, tol=1e-7)
+    want = sq_array_permeability(L, a)
+    for kernel in ("simple", "tiled"):
+        with Tau1(9, (L, L, 1), storage=storage, periodic=(1, 1, 1), g=g, kernel=kernel) as t:
+            t.set_geometry(solid)
+            t.step(steps)
+            if storage in ("f64", "f32"):
+                k = t.reduce()["permeability"]
+                tol = 1e-10 if storage == "f64" else 1e-4
+            else:
+                ks = []
+                for _ in range(20):
+                    t.step(50)
+                    ks.append(t.reduce()["permeability"])
+                k = float(np.mean(ks))
+                tol = 1e-2
+        assert abs(k - ref["permeability"]) <= tol * abs(ref["permeability"]), (storage, kernel, k, ref)
+        assert abs(k / want - 1.0) < 0.03, (storage, kernel, k, want)
