@@ -157,6 +157,22 @@ def bytes_per_fluid_node(storage: str, q: int = 19) -> int:
     return 2 * (d + 1) * s
 
 
+# The paper's own figures for exactly a workload this bench can run (Table
+# tab:perf_comp): D2Q9 Tau1 on a dense 4000^2 plane, best thread count, on a
+# Core i9-12900K (68 GB/s measured). CPU numbers: context for vs_baseline,
+# not a target. The bench's plane adds two solid rows (0.05 % of the nodes).
+PAPER_FIGURES = {(9, 4000, "dense", "f32"): 1.981, (9, 4000, "dense", "f64"): 1.020}
+
+
+def paper_baseline(args):
+    """(GFLUPS, source) of the paper's figure for this exact workload, or None."""
+    v = PAPER_FIGURES.get((args.q, args.size, args.layout, args.storage))
+    if v is None:
+        return None
+    return {"value": v, "unit": "GFLUPS", "hardware": "Core i9-12900K (CPU, 68 GB/s measured)",
+            "source": "Table tab:perf_comp, D2Q9 on 4000^2"}
+
+
 TILED_KERNEL_SOURCES = ("tau1_tiled.cu", "tau1_tiled_tma.cu", "tau1_rowpair.cu", "rowpair.cuh", "tile_column.cuh",
                         "tma.cuh", "tau1_node.cuh", "pack2.cuh", "common.cuh", "lattice.cuh", "static_for.cuh",
                         "kernels.h")
@@ -415,6 +431,10 @@ def run_ours(args):
         "stats": {"permeability": stats["permeability"], "max_abs_u": stats["max_abs_u"]},
         "serve": serve_out,
     }
+    paper = paper_baseline(args)
+    if paper is not None:
+        line["vs_baseline"] = value / paper["value"]
+        line["baseline"] = paper
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args, solid, args.cpu_steps)
     print(json.dumps(line), flush=True)

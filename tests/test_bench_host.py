@@ -60,3 +60,25 @@ def test_reference_arm_on_a_nonzero_rank_does_no_work():
 @pytest.mark.parametrize("storage,b", (("f64", 64), ("f32", 32), ("f16s", 16), ("bf16s", 16)))
 def test_bytes_per_fluid_node(storage, b):
     assert bench_module().bytes_per_fluid_node(storage) == b
+
+
+def test_paper_baseline_only_for_the_papers_exact_workload():
+    """vs_baseline divides by the paper's figure only where Table
+    tab:perf_comp has one for the same lattice, size, layout and precision
+    (D2Q9 on a 4000^2 plane, FP32 1981 and FP64 1020 MFLUPS); the default
+    256^3 porous D3Q19 workload has none."""
+    import types
+
+    b = bench_module()
+
+    def a(**kw):
+        base = dict(q=19, size=256, layout="dense", storage="f32")
+        base.update(kw)
+        return types.SimpleNamespace(**base)
+
+    assert b.paper_baseline(a()) is None
+    assert b.paper_baseline(a(q=9, size=4000))["value"] == 1.981
+    assert b.paper_baseline(a(q=9, size=4000, storage="f64"))["value"] == 1.020
+    assert b.paper_baseline(a(q=9, size=4000, storage="f16s")) is None
+    assert b.paper_baseline(a(q=9, size=2000)) is None
+    assert b.paper_baseline(a(q=9, size=4000, layout="sparse")) is None
