@@ -29,6 +29,7 @@ MUTANTS = {
     "no division by rho": ("double r = 1.0 / (1.0 + d_acc);", "double r = 1.0;"),
     "momentum sign": ("jx += (double)L->c[k][0] * f;", "jx -= (double)L->c[k][0] * f;"),
     "edge weight": ("W19[4] = {1.0 / 3.0, 1.0 / 18.0, 1.0 / 36.0", "W19[4] = {1.0 / 3.0, 1.0 / 18.0, 1.0 / 35.0"),
+    "D3Q27 corner weight": ("1.0 / 54.0, 1.0 / 216.0}", "1.0 / 54.0, 1.0 / 200.0}"),
     "D2Q9 diagonal weight": ("W9[4] = {4.0 / 9.0, 1.0 / 9.0, 1.0 / 36.0", "W9[4] = {4.0 / 9.0, 1.0 / 9.0, 1.0 / 32.0"),
     "Zou-He factor of the outgoing sum": ("- h0 - 2.0 * hout", "- h0 - 1.0 * hout"),
     "Zou-He face sign": ("if (pos[a] == 0) { sgn = 1.0;", "if (pos[a] == 0) { sgn = -1.0;"),
