@@ -571,7 +571,7 @@ def test_zou_he_faces_hold_density_and_normal_flow():
     assert np.all(out[0][solid != 0] == 0.0)
 
 
-@pytest.mark.parametrize("q", [9, 19])
+@pytest.mark.parametrize("q", [9, 19, 27])
 def test_zou_he_channel_matches_poiseuille(q):
     """Pressure-driven channel, run to steady state: H = 20 fluid rows between
     halfway bounce-back walls (wall positions at 1/2 and 20.5), faces at
